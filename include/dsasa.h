@@ -1,0 +1,139 @@
+/*
+ * dsasa.h - C ABI of the GB300 dSASA library (libdsasa.so).
+ *
+ * Computes, for N atoms with centres p_i and radii r_i, the solvent accessible surface
+ * area A_i of every atom and the gradient of sum_i w_i A_i with respect to the centres,
+ * by the exact inclusion-exclusion method of the paper (Sec. "dSASA: an analytical method
+ * for SASA"):
+ *   - weighted points p'_i = (p_i, d_i) with d_i = R_i^2, R_i = fl64(r_i + probe);
+ *   - the weighted Delaunay tetrahedrization (Step 1) is built locally per atom as the
+ *     power (Laguerre) cell L_i clipped by the atom's overlapping neighbours;
+ *   - the dual complex C (Step 2) is its alpha = 0 subcomplex: a simplex is in C iff the
+ *     Laguerre-intersection cells LI_i = L_i cap B_i of its vertices intersect;
+ *   - A_i follows Eq. (sainexclu) with the vertex, edge and triangle terms of
+ *     Eqs. (vertex), (phiedge)/(edge) and (trianglev); the gradient follows Eq. (inexclu)
+ *     with Eq. (triangle), evaluated as a per-atom gather (no atomics, deterministic).
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments of dsasa_compute* are DEVICE pointers (cudaMalloc'd or torch CUDA
+ *     tensors) on the context's device, unless the name ends in _host.  The caller owns
+ *     them; the library never frees or retains them past the call.
+ *   - coords: double[n][3], row-major (x, y, z of atom i at coords[3i..3i+2]), Angstrom.
+ *   - radii: double[n], van der Waals radii WITHOUT the probe, Angstrom.
+ *   - areas_out: double[n], A_i in Angstrom^2.  grad_out: double[n][3] or NULL.
+ *   - Work is enqueued on the context's stream and returns immediately.  Argument errors
+ *     are returned synchronously and nothing is enqueued.  Errors found on the device
+ *     (capacity overflow, unresolved exact predicate) are recorded in a device status word
+ *     that dsasa_status_sync() reads; the atoms concerned get NaN outputs.  Nothing aborts,
+ *     nothing calls __trap, every device loop is bounded.
+ *   - The context owns its scratch (cell list, sorted atom copies, status word).  It grows
+ *     scratch on demand unless cfg.max_atoms fixes the capacity (then a larger n returns
+ *     DSASA_ERR_CAPACITY).  With a fixed capacity no call allocates, so calls can be
+ *     captured in a CUDA graph after one warm-up call.
+ *   - A context is not thread-safe; use one context per host thread / stream.
+ */
+#ifndef DSASA_H
+#define DSASA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dsasa_ctx dsasa_ctx;
+
+typedef enum {
+    DSASA_OK = 0,
+    DSASA_ERR_ARG = 1,           /* invalid argument (NULL pointer, n < 0, non-finite probe, ...) */
+    DSASA_ERR_OOM = 2,           /* device allocation failed */
+    DSASA_ERR_CAPACITY = 3,      /* a fixed capacity was exceeded (atoms, neighbours, cell faces) */
+    DSASA_ERR_UNRESOLVED = 4,    /* an exact predicate exceeded its expansion capacity */
+    DSASA_ERR_CUDA = 5,          /* a CUDA runtime call failed (see dsasa_last_error) */
+    DSASA_ERR_UNIMPLEMENTED = 6,
+    DSASA_ERR_DEGENERATE = 7,    /* an exactly degenerate input (tie) was met; outputs valid
+                                    for one consistent tie-break only */
+    DSASA_ERR_INPUT = 8          /* non-finite coordinate or radius found on the device */
+} dsasa_status;
+
+/* Precision of the arithmetic (the predicates that decide which simplices exist are exact
+ * in both modes):
+ *   DSASA_MIXED - area/gradient terms in FP32 (sqrt, atan2 in float), FP64 accumulation;
+ *                 predicates filtered in FP32, then FP64, then exact expansions.
+ *   DSASA_FP64  - every term in FP64; predicates filtered in FP64, then exact. */
+enum { DSASA_MIXED = 0, DSASA_FP64 = 1 };
+
+typedef struct {
+    int precision;      /* DSASA_MIXED or DSASA_FP64 */
+    double skin;        /* extra neighbour-search margin in Angstrom (>= 0); 0 = exact overlap */
+    int64_t max_atoms;  /* fixed capacity in atoms, or 0 to grow on demand */
+    int64_t max_cells;  /* cap on cell-list cells (0 = default 2^22); larger boxes use coarser cells */
+} dsasa_config;
+
+/* Fills cfg with defaults: MIXED, skin 0, grow on demand, default cell cap. */
+void dsasa_default_config(dsasa_config* cfg);
+
+/* Creates a context on `device` (CUDA ordinal) bound to `cuda_stream` (a cudaStream_t, or
+ * NULL for the legacy default stream).  cfg may be NULL (defaults).  On success *out holds
+ * the context (free it with dsasa_destroy). */
+dsasa_status dsasa_create(dsasa_ctx** out, int device, void* cuda_stream, const dsasa_config* cfg);
+
+/* Rebinds the context to another stream of the same device. */
+dsasa_status dsasa_set_stream(dsasa_ctx* ctx, void* cuda_stream);
+
+/* Changes the precision mode (DSASA_MIXED / DSASA_FP64) of later calls. */
+dsasa_status dsasa_set_precision(dsasa_ctx* ctx, int precision);
+
+/* SASA per atom and, if grad_out != NULL, grad_out[j] = d(sum_i A_i)/d(p_j).
+ * Paper: Eqs. (sainexclu) and (inexclu).  n = 0 is valid (nothing is enqueued). */
+dsasa_status dsasa_compute(dsasa_ctx* ctx, const double* coords, const double* radii, double probe,
+                           int64_t n, double* areas_out, double* grad_out);
+
+/* As dsasa_compute, with grad_out[j] = d(sum_i w_i A_i)/d(p_j) for area_weights w
+ * (double[n], device; NULL means all ones).  This vector-Jacobian product is what
+ * reverse-mode differentiation of an energy sum_i gamma_i A_i needs. */
+dsasa_status dsasa_compute_vjp(dsasa_ctx* ctx, const double* coords, const double* radii, double probe,
+                               int64_t n, const double* area_weights, double* areas_out, double* grad_out);
+
+/* Several independent molecules in one launch.  Molecule m owns atoms
+ * [atom_offsets[m], atom_offsets[m+1]) of the concatenated device arrays; atom_offsets is a
+ * HOST array of n_mol + 1 increasing values starting at 0.  Atoms of different molecules
+ * never interact.  area_weights may be NULL; grad_out may be NULL. */
+dsasa_status dsasa_compute_batch(dsasa_ctx* ctx, int n_mol, const int64_t* atom_offsets,
+                                 const double* coords, const double* radii, double probe,
+                                 const double* area_weights, double* areas_out, double* grad_out);
+
+/* End-to-end convenience on HOST buffers: copies coords/radii/weights to the device, runs
+ * dsasa_compute_vjp, copies areas (and grad if grad_host != NULL) back and synchronises
+ * the stream.  Host buffers may be pageable or pinned; weights_host may be NULL. */
+dsasa_status dsasa_compute_host(dsasa_ctx* ctx, const double* coords_host, const double* radii_host,
+                                double probe, int64_t n, const double* weights_host,
+                                double* areas_host, double* grad_host);
+
+/* Synchronises the context's stream and returns the device status of the calls since the
+ * previous dsasa_status_sync (then clears it).  DSASA_OK if every atom was resolved. */
+dsasa_status dsasa_status_sync(dsasa_ctx* ctx);
+
+/* Diagnostic export of the dual complex C as seen by each atom's local cell.  For every atom
+ * i and every simplex of C that contains i, one record of 5 int32 is written to `records`
+ * (device, capacity `max_records`): {i, v0, v1, v2, v3} with the simplex's atom indices in
+ * increasing order and -1 in unused slots (a vertex, an edge, a triangle or a tetrahedron).
+ * *n_records (host) receives the number of records (when it exceeds max_records, only the
+ * first max_records were written and DSASA_ERR_CAPACITY is returned).  Synchronises. */
+dsasa_status dsasa_export_complex(dsasa_ctx* ctx, const double* coords, const double* radii, double probe,
+                                  int64_t n, int32_t* records, int64_t max_records, int64_t* n_records);
+
+/* Message describing the last error of this context ("" if none). */
+const char* dsasa_last_error(const dsasa_ctx* ctx);
+
+/* Releases the context and its scratch.  NULL is a no-op. */
+void dsasa_destroy(dsasa_ctx* ctx);
+
+/* Library version string. */
+const char* dsasa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSASA_H */

@@ -906,7 +906,8 @@ int oracle_tri_term(const double* p1, const double* p2, const double* p3, double
 }
 
 // exact sign predicates exposed for tests: kind 0 orient(a,b,c,d), 1 conflict(a,b,c,d;e),
-// 2 tet psi(a,b,c,d), 3 triangle psi(a,b,c), 4 edge psi(a,b)
+// 2 tet psi(a,b,c,d), 3 triangle psi(a,b,c), 4 edge psi(a,b), 5 e attaches triangle (a,b,c),
+// 6 e attaches edge (a,b), 7 e attaches vertex a (5-7 return 1 when attached, else 0)
 int oracle_predicate(int kind, int npts, const double* xyzR, const int* ids) {
     Geo g;
     g.n = npts;
@@ -922,6 +923,9 @@ int oracle_predicate(int kind, int npts, const double* xyzR, const int* ids) {
         case 2: return g.tet_psi(ids[0], ids[1], ids[2], ids[3]);
         case 3: return g.tri_psi(ids[0], ids[1], ids[2]);
         case 4: return g.edge_psi(ids[0], ids[1]);
+        case 5: return g.tri_attached(ids[0], ids[1], ids[2], ids[3]) ? 1 : 0;
+        case 6: return g.edge_attached(ids[0], ids[1], ids[2]) ? 1 : 0;
+        case 7: return g.vertex_attached(ids[0], ids[1]) ? 1 : 0;
     }
     return 0;
 }

@@ -161,7 +161,8 @@ def tri_term(p1, p2, p3, R1, R2, R3):
 
 
 def predicate(kind: int, pts_xyzR, ids) -> int:
-    """Exact sign predicates: 0 orient, 1 conflict (-1 = conflict), 2 tet psi, 3 tri psi, 4 edge psi."""
+    """Exact sign predicates: 0 orient, 1 conflict (-1 = conflict), 2 tet psi, 3 tri psi, 4 edge psi,
+    5/6/7 attachment of a triangle / edge / vertex by the last point (1 = attached)."""
     lib = _load()
     a = np.ascontiguousarray(pts_xyzR, dtype=np.float64).reshape(-1, 4)
     idx = np.ascontiguousarray(ids, dtype=np.int32)

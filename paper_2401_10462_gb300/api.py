@@ -1,0 +1,224 @@
+"""Thin ctypes binding of libdsasa.so (include/dsasa.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module passes device
+pointers of torch CUDA tensors (or host numpy buffers for ``dsasa_compute_host``) and the
+current torch stream.  There is no CPU fallback: if the library is missing, importing
+this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build.LIB
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+DSASA_OK = 0
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CAPACITY", 4: "ERR_UNRESOLVED", 5: "ERR_CUDA",
+                6: "ERR_UNIMPLEMENTED", 7: "ERR_DEGENERATE", 8: "ERR_INPUT"}
+DSASA_MIXED, DSASA_FP64 = 0, 1
+PROBE = 1.4
+
+
+class dsasa_config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("skin", ctypes.c_double), ("max_atoms", ctypes.c_int64),
+                ("max_cells", ctypes.c_int64)]
+
+
+_vp, _dp, _i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+_lib.dsasa_default_config.argtypes = [ctypes.POINTER(dsasa_config)]
+_lib.dsasa_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.POINTER(dsasa_config)]
+_lib.dsasa_set_stream.argtypes = [_vp, _vp]
+_lib.dsasa_set_precision.argtypes = [_vp, ctypes.c_int]
+_lib.dsasa_compute.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp]
+_lib.dsasa_compute_vjp.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp, _vp]
+_lib.dsasa_compute_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _vp, _vp, ctypes.c_double,
+                                     _vp, _vp, _vp]
+_lib.dsasa_compute_host.argtypes = [_vp, _dp, _dp, ctypes.c_double, _i64, _dp, _dp, _dp]
+_lib.dsasa_status_sync.argtypes = [_vp]
+_lib.dsasa_export_complex.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_int64)]
+_lib.dsasa_last_error.argtypes = [_vp]
+_lib.dsasa_last_error.restype = ctypes.c_char_p
+_lib.dsasa_destroy.argtypes = [_vp]
+_lib.dsasa_version.restype = ctypes.c_char_p
+for _f in ("dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute", "dsasa_compute_vjp",
+           "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync", "dsasa_export_complex"):
+    getattr(_lib, _f).restype = ctypes.c_int
+
+EXPORTED = ("dsasa_default_config", "dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute",
+            "dsasa_compute_vjp", "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync",
+            "dsasa_export_complex", "dsasa_last_error", "dsasa_destroy", "dsasa_version")
+
+
+class DSASAError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dsasa {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def version() -> str:
+    return _lib.dsasa_version().decode()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _check_tensor(t, name, n, width=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    shape = (n,) if width is None else (n, width)
+    if tuple(t.shape) != shape:
+        raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+
+
+class Context:
+    """One dsasa_ctx bound to a device and a stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream=None, precision: str | int = "mixed", skin: float = 0.0,
+                 max_atoms: int = 0, max_cells: int = 0):
+        cfg = dsasa_config()
+        _lib.dsasa_default_config(ctypes.byref(cfg))
+        cfg.precision = precision if isinstance(precision, int) else {"mixed": DSASA_MIXED, "fp64": DSASA_FP64}[precision]
+        cfg.skin = float(skin)
+        cfg.max_atoms = int(max_atoms)
+        cfg.max_cells = int(max_cells)
+        self.device = device
+        h = _vp()
+        st = _lib.dsasa_create(ctypes.byref(h), device, _vp(self._stream_handle(stream)), ctypes.byref(cfg))
+        if st != DSASA_OK:
+            raise DSASAError(st, "dsasa_create failed")
+        self._h = h
+        self._stream = stream
+
+    @staticmethod
+    def _stream_handle(stream):
+        if stream is None:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        if isinstance(stream, int):
+            return stream
+        return stream.cuda_stream
+
+    def _sync_stream(self):
+        if self._stream is None:
+            _lib.dsasa_set_stream(self._h, _vp(self._stream_handle(None)))
+
+    def _raise(self, st):
+        if st != DSASA_OK:
+            raise DSASAError(st, _lib.dsasa_last_error(self._h).decode())
+
+    def set_precision(self, precision):
+        p = precision if isinstance(precision, int) else {"mixed": DSASA_MIXED, "fp64": DSASA_FP64}[precision]
+        self._raise(_lib.dsasa_set_precision(self._h, p))
+
+    def compute(self, coords, radii, areas_out, grad_out=None, weights=None, probe: float = PROBE):
+        """dsasa_compute_vjp on device tensors (asynchronous on the stream)."""
+        n = int(coords.shape[0])
+        _check_tensor(coords, "coords", n, 3)
+        _check_tensor(radii, "radii", n)
+        _check_tensor(areas_out, "areas_out", n)
+        if grad_out is not None:
+            _check_tensor(grad_out, "grad_out", n, 3)
+        if weights is not None:
+            _check_tensor(weights, "weights", n)
+        self._sync_stream()
+        self._raise(_lib.dsasa_compute_vjp(self._h, _ptr(coords), _ptr(radii), float(probe), n, _ptr(weights),
+                                           _ptr(areas_out), _ptr(grad_out)))
+
+    def compute_batch(self, offsets, coords, radii, areas_out, grad_out=None, weights=None, probe: float = PROBE):
+        """dsasa_compute_batch: molecule m owns atoms [offsets[m], offsets[m+1])."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        n = int(off[-1])
+        _check_tensor(coords, "coords", n, 3)
+        _check_tensor(radii, "radii", n)
+        _check_tensor(areas_out, "areas_out", n)
+        self._sync_stream()
+        self._raise(_lib.dsasa_compute_batch(self._h, len(off) - 1, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                             _ptr(coords), _ptr(radii), float(probe), _ptr(weights), _ptr(areas_out),
+                                             _ptr(grad_out)))
+
+    def compute_host(self, coords, radii, weights=None, grad: bool = True, probe: float = PROBE, out=None):
+        """dsasa_compute_host on numpy buffers: copies in, computes, copies out, synchronises."""
+        xyz = np.ascontiguousarray(coords, dtype=np.float64)
+        r = np.ascontiguousarray(radii, dtype=np.float64)
+        n = xyz.shape[0]
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+        if out is None:
+            a = np.empty(n)
+            g = np.empty((n, 3)) if grad else None
+        else:
+            a, g = out
+        self._sync_stream()
+        dp = lambda x: None if x is None else x.ctypes.data_as(_dp)
+        self._raise(_lib.dsasa_compute_host(self._h, dp(xyz), dp(r), float(probe), n, dp(w), dp(a), dp(g)))
+        return a, g
+
+    def status_sync(self):
+        """Synchronise and raise if a device-side error was recorded since the last call."""
+        self._raise(_lib.dsasa_status_sync(self._h))
+
+    def status_code(self) -> int:
+        return _lib.dsasa_status_sync(self._h)
+
+    def export_complex(self, coords, radii, probe: float = PROBE, max_records: int = None):
+        """Records (owner, v0, v1, v2, v3) of every simplex of C seen by every atom's cell."""
+        import torch
+        n = int(coords.shape[0])
+        cap = max_records or 64 * n + 64
+        rec = torch.empty((cap, 5), dtype=torch.int32, device=coords.device)
+        cnt = ctypes.c_int64(0)
+        self._sync_stream()
+        st = _lib.dsasa_export_complex(self._h, _ptr(coords), _ptr(radii), float(probe), n, _ptr(rec), cap,
+                                       ctypes.byref(cnt))
+        self._raise(st)
+        return rec[: cnt.value]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dsasa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx = {}
+
+
+def default_context(device: int = 0, precision: str = "mixed") -> Context:
+    key = (device, precision)
+    if key not in _default_ctx:
+        _default_ctx[key] = Context(device=device, precision=precision)
+    return _default_ctx[key]
+
+
+def sasa(coords, radii, probe: float = PROBE, weights=None, grad: bool = True, precision: str = "mixed",
+         check: bool = True):
+    """SASA per atom (and d(sum w_i A_i)/dx) for CUDA float64 tensors; returns (areas, grad)."""
+    import torch
+    ctx = default_context(coords.device.index or 0, precision)
+    n = coords.shape[0]
+    areas = torch.empty(n, dtype=torch.float64, device=coords.device)
+    g = torch.empty((n, 3), dtype=torch.float64, device=coords.device) if grad else None
+    ctx.compute(coords.contiguous(), radii.contiguous(), areas, g, weights, probe)
+    if check:
+        ctx.status_sync()
+    return areas, g

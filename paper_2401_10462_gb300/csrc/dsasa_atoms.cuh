@@ -1,0 +1,861 @@
+// The per-atom kernel: one warp builds atom i's restricted Laguerre cell, classifies the
+// simplices of the dual complex C that contain i, and evaluates A_i and the gradient entry
+// of atom i.  Nothing goes through global memory between these steps.
+//
+//   Step 1 (paper): the weighted Delaunay tetrahedra around i are the vertices of the power
+//     cell L_i.  The warp starts from a cube (6 ghost planes at distance h > R_i) and clips
+//     it by the power bisector of every neighbour whose ball overlaps B_i (all other
+//     neighbours cannot cut L_i inside B_i, so L_i cap B_i is exact).  The cell is stored as
+//     its dual triangulation: a vertex = a triangle (a, b, c) of plane ids, counter-clockwise
+//     seen from outside, with the three adjacent triangles.  Clipping by plane m removes the
+//     vertices strictly beyond m (an exact predicate), and re-triangulates the hole with a
+//     fan around m along the boundary cycle of the removed region.
+//   Step 2: a cell vertex (a,b,c) is a tetrahedron of C iff it lies in B_i (psi <= 0); a cell
+//     edge (a,b) is a triangle of C iff it meets B_i (its orthocentre lies on it with psi <= 0,
+//     or an end vertex is in C); a face a is an edge of C iff it meets B_i; i is a vertex of C
+//     iff its cell meets B_i.  A vertex / edge / triangle whose tetrahedra close around it is
+//     interior (coefficient exactly 0, skipped).
+//   Step 3: A_i by Eq. (sainexclu); the gradient entry of atom i gathers, over the simplices
+//     of C containing i, the derivative of every atom's terms (Eq. inexclu) - no atomics.
+//
+// One warp per atom; the cell lives in shared memory (plane table, triangle table) and in
+// registers (each lane caches the homogeneous coordinates of up to 4 cell vertices).
+#pragma once
+#include "dsasa_kernels.cuh"
+#include "dsasa_math.cuh"
+
+#include <stdint.h>
+
+namespace dsasa {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int NE = 128;          // plane entries: 0..5 ghosts, 6.. candidates
+constexpr int NG = 6;
+constexpr int KMAX = NE - NG;    // overlapping neighbours per atom
+constexpr int NT = 128;          // cell-vertex slots (4 per lane)
+constexpr int SPL = NT / 32;
+constexpr uint8_t NONE = 0xff;
+constexpr int WARPS = 4;         // warps per block
+
+template <class R> struct Smem {
+    R pq[NE][4];          // plane q.x, q.y, q.z, b (relative to p_i)
+    R pB[NE];             // magnitude proxy of b for the filters
+    int pg[NE];           // global atom index (>= 0) or -1 - ghost id
+    uint8_t start[NE];    // a vertex slot on the face of this plane
+    uint8_t bnext[NE], bprev[NE], bslot[NE], bkept[NE], bkedge[NE];
+    uint8_t ord[NE];      // clipping order (entry ids)
+    uint8_t eflag[NE];    // face summary: bit0 edge in C, bit1 interior (closed)
+    R ephi[NE];           // Phi_ia of the face
+    uchar4 tv[NT];        // cell vertex = triangle of plane ids (x = NONE: dead slot)
+    uchar4 ta[NT];        // neighbour slots across edges (v0 v1), (v1 v2), (v2 v0)
+    uint8_t kf[NT];       // 0 not in C, 1 tetrahedron of C, 2 involves a ghost plane
+    unsigned tf[NT];      // bit k: the triangle of edge k is in C; bit 4+k: it is processed here
+    unsigned skey[NE];    // orderable sort key of each candidate
+    uint8_t rem[NT];
+    uint8_t rsl[NT];      // removed slots in order
+    uint8_t fs[NT];       // free slot stack
+    int hw, nfree, bad;
+};
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ uint8_t tv_get(const uchar4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+__device__ __forceinline__ void ta_set(Smem<float>* S, int t, int k, uint8_t s) { ((uint8_t*)&S->ta[t & (NT - 1)])[k] = s; }
+__device__ __forceinline__ void ta_set(Smem<double>* S, int t, int k, uint8_t s) { ((uint8_t*)&S->ta[t & (NT - 1)])[k] = s; }
+
+// ------------------------------------------------------------------ global plane access
+struct Ctx {
+    const double* xyz;
+    const double* R;
+    double pi[3];
+    double Ri;
+    double h;
+    int i;
+    int* status;
+};
+
+__device__ void plane64_of(const Ctx& c, int g, double q[3], double& b, double& babs, bool& exact) {
+    if (g < 0) {
+        ghost_plane64(-1 - g, c.h, q, b);
+        babs = fabs(b);
+        exact = true;
+        return;
+    }
+    double pk[3] = {c.xyz[3 * g], c.xyz[3 * g + 1], c.xyz[3 * g + 2]};
+    plane64(c.pi, c.Ri, pk, c.R[g], q, b, babs);
+    exact = false;
+}
+__device__ PlaneN<FA<double>> fa64_of(const Ctx& c, int g) {
+    double q[3], b, babs;
+    bool ex;
+    plane64_of(c, g, q, b, babs, ex);
+    return fa_plane64(q, b, babs, ex);
+}
+__device__ PlaneN<XP> xp_of(const Ctx& c, int g) {
+    if (g < 0) return xp_ghost(-1 - g, c.h);
+    double pk[3] = {c.xyz[3 * g], c.xyz[3 * g + 1], c.xyz[3 * g + 2]};
+    return xp_plane(c.pi, c.Ri, pk, c.R[g]);
+}
+
+// predicate kinds
+enum { PK_CLIP = 0, PK_TET = 1, PK_TRI = 2, PK_TRIB = 3, PK_EDGE = 4, PK_EDGEB = 5, PK_VERT = 6 };
+
+template <class N> __device__ N eval_kind(int kind, const PlaneN<N>* P, const N& wi) {
+    switch (kind) {
+        case PK_CLIP: return pred_clip(P[0], P[1], P[2], P[3]);
+        case PK_TET: return pred_tet_psi(P[0], P[1], P[2], wi);
+        case PK_TRI: return pred_tri_psi(P[0], P[1], wi);
+        case PK_TRIB: return pred_tri_beyond(P[0], P[1], P[2]);
+        case PK_EDGE: return pred_edge_psi(P[0], wi);
+        case PK_EDGEB: return pred_edge_beyond(P[0], P[1]);
+        default: return P[0].b;
+    }
+}
+__device__ __forceinline__ int kind_planes(int kind) {
+    return kind == PK_CLIP ? 4 : (kind == PK_TET || kind == PK_TRIB) ? 3 : (kind == PK_TRI || kind == PK_EDGEB) ? 2 : 1;
+}
+
+// Slow path: FP64 filter (unless skip64), then exact expansions.  Never returns an
+// undecided sign except for an exact zero (a tie, reported as degenerate).
+__device__ __noinline__ int resolve_exact(const Ctx& c, int kind, int g0, int g1, int g2, int g3, bool try64) {
+    int gs[4] = {g0, g1, g2, g3};
+    int np = kind_planes(kind);
+    if (try64) {
+        PlaneN<FA<double>> P[4];
+        for (int k = 0; k < np; ++k) P[k] = fa64_of(c, gs[k]);
+        FA<double> wi = {c.Ri * c.Ri, c.Ri * c.Ri};
+        int s = fa_sign(eval_kind(kind, P, wi), G64, TINY64);
+        if (s != 0) return s;
+    }
+    PlaneN<XP> P[4];
+    for (int k = 0; k < np; ++k) P[k] = xp_of(c, gs[k]);
+    XP wi = xp_sq(c.Ri);
+    XP v = eval_kind(kind, P, wi);
+    if (v.ovf) {
+        atomicOr(c.status, ST_UNRESOLVED);
+        return v.n ? (v.c[v.n - 1] > 0 ? 1 : -1) : 0;
+    }
+    int s = xp_sign(v);
+    if (s == 0) atomicOr(c.status, ST_DEGENERATE);
+    return s;
+}
+
+// filter planes from the shared table
+template <class R> __device__ __forceinline__ PlaneN<FA<R>> fplane(const Smem<R>* S, int e) {
+    e &= NE - 1;
+    PlaneN<FA<R>> P;
+    P.q = {{S->pq[e][0], fabs(S->pq[e][0])}, {S->pq[e][1], fabs(S->pq[e][1])}, {S->pq[e][2], fabs(S->pq[e][2])}};
+    P.b = {S->pq[e][3], S->pB[e]};
+    return P;
+}
+template <class R> struct Gam;
+template <> struct Gam<float> {
+    static constexpr float g = G32, gclip = G32_CLIP, tiny = TINY32;
+    static constexpr bool try64 = true;
+};
+template <> struct Gam<double> {
+    static constexpr double g = G64, gclip = G64, tiny = TINY64;
+    static constexpr bool try64 = false;
+};
+
+template <int KIND, class N> __device__ __forceinline__ N eval_k(const PlaneN<N>* P, const N& wi) {
+    if constexpr (KIND == PK_CLIP) return pred_clip(P[0], P[1], P[2], P[3]);
+    else if constexpr (KIND == PK_TET) return pred_tet_psi(P[0], P[1], P[2], wi);
+    else if constexpr (KIND == PK_TRI) return pred_tri_psi(P[0], P[1], wi);
+    else if constexpr (KIND == PK_TRIB) return pred_tri_beyond(P[0], P[1], P[2]);
+    else if constexpr (KIND == PK_EDGE) return pred_edge_psi(P[0], wi);
+    else if constexpr (KIND == PK_EDGEB) return pred_edge_beyond(P[0], P[1]);
+    else return P[0].b;
+}
+
+// sign of predicate KIND on shared-table planes e0..e3 (FP32/FP64 filter, then slow path)
+template <int KIND, class R> __device__ int psign(const Smem<R>* S, const Ctx& c, const FA<R>& wi, int e0, int e1, int e2 = 0, int e3 = 0) {
+    PlaneN<FA<R>> P[4] = {fplane(S, e0), fplane(S, e1), fplane(S, e2), fplane(S, e3)};
+    int s = fa_sign(eval_k<KIND>(P, wi), Gam<R>::g, Gam<R>::tiny);
+    if (s != 0) return s;
+    const int kind = KIND;
+    return resolve_exact(c, kind, S->pg[e0 & (NE - 1)], S->pg[e1 & (NE - 1)], S->pg[e2 & (NE - 1)],
+                         S->pg[e3 & (NE - 1)], Gam<R>::try64);
+}
+
+template <class R> __device__ __forceinline__ P3<R> ppos(const Smem<R>* S, int e) {
+    e &= NE - 1;
+    return {S->pq[e][0], S->pq[e][1], S->pq[e][2]};
+}
+
+// ------------------------------------------------------------------ the kernel
+template <class R, bool GRAD>
+__global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
+    const bool EXPORT = A.rec != nullptr;
+    __shared__ Smem<R> smem_all[WARPS];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    Smem<R>* S = &smem_all[wib];
+    const int nwarps = gridDim.x * WARPS;
+    const R PI = pi_t<R>();
+
+    for (int s = blockIdx.x * WARPS + wib; s < A.n; s += nwarps) {
+        const int i = A.sidx[s];
+        const float4 fi = A.sf4[s];
+        const MolGrid G = A.grids[A.molid[i]];
+        Ctx c;
+        c.xyz = A.xyz;
+        c.R = A.R;
+        c.pi[0] = A.xyz[3 * i];
+        c.pi[1] = A.xyz[3 * i + 1];
+        c.pi[2] = A.xyz[3 * i + 2];
+        c.Ri = A.R[i];
+        c.h = ghost_h(c.Ri);
+        c.i = i;
+        c.status = A.status;
+        const R Rr = (R)c.Ri;
+        const FA<R> wi = {Rr * Rr, Rr * Rr};
+
+        // ---------------- neighbour candidates: balls that may overlap B_i
+        int nc = 0;
+        {
+            int cx = min(max((int)floorf((fi.x - G.lo[0]) * G.inv_cell), 0), G.dims[0] - 1);
+            int cy = min(max((int)floorf((fi.y - G.lo[1]) * G.inv_cell), 0), G.dims[1] - 1);
+            int cz = min(max((int)floorf((fi.z - G.lo[2]) * G.inv_cell), 0), G.dims[2] - 1);
+            for (int dz = -1; dz <= 1; ++dz) {
+                int z = cz + dz;
+                if (z < 0 || z >= G.dims[2]) continue;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    int y = cy + dy;
+                    if (y < 0 || y >= G.dims[1]) continue;
+                    int row = G.base + (z * G.dims[1] + y) * G.dims[0];
+                    int x0 = max(cx - 1, 0), x1 = min(cx + 1, G.dims[0] - 1);
+                    int beg = A.cstart[row + x0], end = A.cstart[row + x1 + 1];
+                    for (int b0 = beg; b0 < end; b0 += 32) {
+                        int k = b0 + lane;
+                        bool ok = false;
+                        int j = -1;
+                        if (k < end) {
+                            float4 fj = A.sf4[k];
+                            j = A.sidx[k];
+                            float dx = fj.x - fi.x, dy2 = fj.y - fi.y, dz2 = fj.z - fi.z;
+                            float rr = fi.w + fj.w + G.margin;
+                            ok = (j != i) && (dx * dx + dy2 * dy2 + dz2 * dz2 < rr * rr);
+                        }
+                        unsigned bal = __ballot_sync(FULL, ok);
+                        int pos = nc + __popc(bal & lanemask_lt());
+                        if (ok && pos < KMAX) S->pg[NG + pos] = j;
+                        nc += __popc(bal);
+                    }
+                }
+            }
+        }
+        if (nc > KMAX) {
+            if (lane == 0) {
+                atomicOr(A.status, ST_CAND_OVF);
+                A.areas[i] = __longlong_as_double(0x7ff8000000000000ll);
+                if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
+            }
+            __syncwarp();
+            continue;
+        }
+
+        // ---------------- plane table: ghosts 0..5, candidates NG..NG+nc-1; sort keys
+        unsigned long long key[SPL];
+        unsigned pay[SPL];
+        for (int r = 0; r < SPL; ++r) { key[r] = ~0ull; pay[r] = 0; }
+        for (int e = lane; e < NG + nc; e += 32) {
+            double q[3], b, babs;
+            bool ex;
+            int g = e < NG ? -1 - e : S->pg[e];
+            plane64_of(c, g, q, b, babs, ex);
+            if (e < NG) S->pg[e] = g;
+            for (int k = 0; k < 3; ++k) S->pq[e][k] = (R)q[k];
+            S->pq[e][3] = (R)b;
+            if (sizeof(R) == 4) S->pB[e] = (R)(fabs((double)(float)b) * (1.0 + 1.2e-7) + babs * 1.4901161193847656e-08);
+            else S->pB[e] = (R)(ex ? fabs(b) : 8.0 * babs);
+            S->start[e] = NONE;
+            if (e >= NG) {
+                // sort key: signed distance of the bisector from p_i (ties: atom index)
+                float kf = (float)(b / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + 1e-300));
+                unsigned u = __float_as_uint(kf);
+                S->skey[e] = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+            }
+            S->eflag[e] = 0;
+        }
+        __syncwarp();
+        for (int r = 0; r < SPL; ++r) {
+            int el = r * 32 + lane;
+            if (el < nc) {
+                key[r] = ((unsigned long long)S->skey[NG + el] << 32) | (unsigned)S->pg[NG + el];
+                pay[r] = NG + el;
+            }
+        }
+        __syncwarp();
+        // bitonic sort of 128 (key, payload) pairs, element e = r*32 + lane
+        for (int k = 2; k <= NT; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                if (j >= 32) {
+                    int jr = j >> 5;
+#pragma unroll
+                    for (int r = 0; r < SPL; ++r) {
+                        int r2 = r ^ jr;
+                        if (r2 > r) {
+                            int e = r * 32 + lane;
+                            bool up = (e & k) == 0;
+                            bool sw = up ? (key[r] > key[r2]) : (key[r] < key[r2]);
+                            if (sw) {
+                                unsigned long long tk = key[r]; key[r] = key[r2]; key[r2] = tk;
+                                unsigned tp = pay[r]; pay[r] = pay[r2]; pay[r2] = tp;
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < SPL; ++r) {
+                        int e = r * 32 + lane;
+                        unsigned long long ok = __shfl_xor_sync(FULL, key[r], j);
+                        unsigned op = __shfl_xor_sync(FULL, pay[r], j);
+                        bool up = (e & k) == 0;
+                        bool lower = (lane & j) == 0;
+                        bool take = (lower == up) ? (ok < key[r]) : (ok > key[r]);
+                        if (take) { key[r] = ok; pay[r] = op; }
+                    }
+                }
+            }
+        }
+        // renumber the candidate planes in sorted order, so that every later summation
+        // order depends only on the geometry (not on the order atoms sit in their cells)
+        {
+            R tq[SPL][4], tb[SPL];
+            int tg[SPL];
+#pragma unroll
+            for (int r = 0; r < SPL; ++r) {
+                int e = r * 32 + lane;
+                if (e < nc) {
+                    int src = pay[r] & (NE - 1);
+                    for (int k = 0; k < 4; ++k) tq[r][k] = S->pq[src][k];
+                    tb[r] = S->pB[src];
+                    tg[r] = S->pg[src];
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < SPL; ++r) {
+                int e = r * 32 + lane;
+                if (e < nc) {
+                    for (int k = 0; k < 4; ++k) S->pq[NG + e][k] = tq[r][k];
+                    S->pB[NG + e] = tb[r];
+                    S->pg[NG + e] = tg[r];
+                    S->ord[e] = (uint8_t)(NG + e);
+                }
+            }
+            __syncwarp();
+        }
+
+        // ---------------- initial cell: the cube of the 6 ghost planes (8 vertices)
+        for (int t = lane; t < NT; t += 32) {
+            uchar4 v = make_uchar4(NONE, NONE, NONE, 0);
+            if (t < 8) {
+                int sx = (t & 1) ? -1 : 1, sy = (t & 2) ? -1 : 1, sz = (t & 4) ? -1 : 1;
+                uint8_t px = sx > 0 ? 0 : 1, py = sy > 0 ? 2 : 3, pz = sz > 0 ? 4 : 5;
+                v = (sx * sy * sz > 0) ? make_uchar4(px, py, pz, 0) : make_uchar4(py, px, pz, 0);
+            }
+            S->tv[t] = v;
+            S->rem[t] = 0;
+            S->kf[t] = 0;
+            S->tf[t] = 0;
+        }
+        if (lane == 0) { S->hw = 8; S->nfree = 0; S->bad = 0; }
+        __syncwarp();
+        if (lane < 8) {
+            uchar4 v = S->tv[lane];
+            uchar4 adj = make_uchar4(NONE, NONE, NONE, 0);
+            for (int k = 0; k < 3; ++k) {
+                uint8_t a = tv_get(v, k), b = tv_get(v, (k + 1) % 3);
+                for (int t2 = 0; t2 < 8; ++t2) {
+                    uchar4 w = S->tv[t2];
+                    for (int k2 = 0; k2 < 3; ++k2)
+                        if (tv_get(w, k2) == b && tv_get(w, (k2 + 1) % 3) == a) ((uint8_t*)&adj)[k] = (uint8_t)t2;
+                }
+            }
+            S->ta[lane] = adj;
+        }
+        if (lane < NG) S->start[lane] = (lane & 1) ? 7 : 0;   // +x,+y,+z at corner 0; -x,-y,-z at 7
+        __syncwarp();
+
+        // per-lane vertex caches (homogeneous z = Dv / D with magnitudes for the filter)
+        R V[SPL][4], Va[SPL][4];
+        unsigned alive = 0;
+        auto compute_vertex = [&](int r, int t) {
+            uchar4 v = S->tv[t];
+            PlaneN<FA<R>> Pa = fplane(S, v.x), Pb = fplane(S, v.y), Pc = fplane(S, v.z);
+            V3<FA<R>> Dv;
+            FA<R> D;
+            vertex_hom(Pa, Pb, Pc, Dv, D);
+            V[r][0] = Dv.x.v; V[r][1] = Dv.y.v; V[r][2] = Dv.z.v; V[r][3] = D.v;
+            Va[r][0] = Dv.x.a; Va[r][1] = Dv.y.a; Va[r][2] = Dv.z.a; Va[r][3] = D.a;
+        };
+#pragma unroll
+        for (int r = 0; r < SPL; ++r) {
+            int t = r * 32 + lane;
+            if (t < 8) { compute_vertex(r, t); alive |= 1u << r; }
+        }
+
+        // ---------------- clipping by the sorted neighbour planes
+        bool empty = false;
+        for (int kk = 0; kk < nc && !empty; ++kk) {
+            const int m = S->ord[kk] & (NE - 1);
+            const PlaneN<FA<R>> M = fplane(S, m);
+            unsigned remv = 0;
+#pragma unroll
+            for (int r = 0; r < SPL; ++r) {
+                if (!(alive >> r & 1)) continue;
+                FA<R> sv;
+                sv.v = M.q.x.v * V[r][0] + M.q.y.v * V[r][1] + M.q.z.v * V[r][2] - M.b.v * V[r][3];
+                sv.a = M.q.x.a * Va[r][0] + M.q.y.a * Va[r][1] + M.q.z.a * Va[r][2] + M.b.a * Va[r][3];
+                int sg = fa_sign(sv, Gam<R>::gclip, Gam<R>::tiny);
+                if (sg == 0) {
+                    uchar4 v = S->tv[r * 32 + lane];
+                    sg = resolve_exact(c, PK_CLIP, S->pg[v.x & (NE - 1)], S->pg[v.y & (NE - 1)], S->pg[v.z & (NE - 1)],
+                                       S->pg[m], Gam<R>::try64);
+                }
+                if (sg > 0) remv |= 1u << r;
+            }
+            unsigned bal[SPL];
+            int nrem = 0, nalive = 0;
+#pragma unroll
+            for (int r = 0; r < SPL; ++r) {
+                bal[r] = __ballot_sync(FULL, remv >> r & 1);
+                nrem += __popc(bal[r]);
+                nalive += __popc(__ballot_sync(FULL, alive >> r & 1));
+            }
+            if (nrem == 0) continue;
+            if (nrem == nalive) { empty = true; break; }
+            // removed flags and the ordered list of removed slots
+            int before = 0;
+#pragma unroll
+            for (int r = 0; r < SPL; ++r) {
+                int t = r * 32 + lane;
+                S->rem[t] = (remv >> r) & 1;
+                if (remv >> r & 1) S->rsl[before + __popc(bal[r] & lanemask_lt())] = (uint8_t)t;
+                before += __popc(bal[r]);
+            }
+            __syncwarp();
+            // boundary edges of the removed region: removed triangle edge (a -> b) whose
+            // neighbour is kept; the new face m gets the triangle (a, b, m)
+            uint8_t myb[12];
+            int mynb = 0;
+#pragma unroll
+            for (int r = 0; r < SPL; ++r) {
+                if (!(remv >> r & 1)) continue;
+                int t = r * 32 + lane;
+                uchar4 v = S->tv[t], adj = S->ta[t];
+                for (int k = 0; k < 3; ++k) {
+                    int t2 = tv_get(adj, k) & (NT - 1);
+                    if (S->rem[t2]) continue;
+                    uint8_t a = tv_get(v, k) & (NE - 1), b = tv_get(v, (k + 1) % 3) & (NE - 1);
+                    uchar4 adj2 = S->ta[t2];
+                    int k2 = adj2.x == t ? 0 : (adj2.y == t ? 1 : 2);
+                    S->bnext[a] = b;
+                    S->bprev[b] = a;
+                    S->bkept[a] = (uint8_t)t2;
+                    S->bkedge[a] = (uint8_t)k2;
+                    if (mynb < 12) myb[mynb++] = a; else S->bad = 1;
+                }
+            }
+            int nb = warp_sum_i(mynb);
+            int off = mynb;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(FULL, off, o);
+                if (lane >= o) off += y;
+            }
+            off -= mynb;
+            const int hw = S->hw, nfree = S->nfree;
+            const int extra = nb - nrem;
+            if (hw + max(0, extra - nfree) > NT) {
+                __syncwarp();
+                if (lane == 0) S->bad = 2;
+                __syncwarp();
+                break;
+            }
+            __syncwarp();
+            for (int q = 0; q < mynb; ++q) {
+                int e = off + q;
+                int slot;
+                if (e < nrem) slot = S->rsl[e];
+                else {
+                    int x = e - nrem;
+                    slot = x < nfree ? S->fs[nfree - 1 - x] : hw + (x - nfree);
+                }
+                S->bslot[myb[q]] = (uint8_t)slot;
+            }
+            __syncwarp();
+            for (int q = 0; q < mynb; ++q) {
+                uint8_t a = myb[q];
+                uint8_t b = S->bnext[a];
+                int sl = S->bslot[a] & (NT - 1);
+                S->tv[sl] = make_uchar4(a, b, (uint8_t)m, 0);
+                S->ta[sl] = make_uchar4(S->bkept[a], S->bslot[b & (NE - 1)], S->bslot[S->bprev[a] & (NE - 1)], 0);
+                ta_set(S, S->bkept[a], S->bkedge[a] & 3, (uint8_t)sl);
+                S->start[a] = (uint8_t)sl;
+                S->rem[sl] = 2;
+            }
+            if (mynb > 0 && off == 0) S->start[m] = S->bslot[myb[0]];
+            __syncwarp();
+            // leftover removed slots become free; update the slot allocator
+            if (extra < 0) {
+                for (int y = lane; y < -extra; y += 32) {
+                    int sl = S->rsl[nb + y];
+                    S->tv[sl] = make_uchar4(NONE, NONE, NONE, 0);
+                    S->fs[nfree + y] = (uint8_t)sl;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                if (extra <= nfree) S->nfree = nfree - extra;
+                else { S->nfree = 0; S->hw = hw + (extra - nfree); }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < SPL; ++r) {
+                int t = r * 32 + lane;
+                uint8_t st = S->rem[t];
+                if (st == 2) { compute_vertex(r, t); alive |= 1u << r; }
+                else if (st == 1) alive &= ~(1u << r);
+                S->rem[t] = 0;
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+        const bool bad = S->bad != 0;
+        if (bad) {
+            if (lane == 0) {
+                atomicOr(A.status, S->bad == 2 ? ST_TRI_OVF : ST_BADCELL);
+                A.areas[i] = __longlong_as_double(0x7ff8000000000000ll);
+                if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
+            }
+            __syncwarp();
+            continue;
+        }
+        if (empty) {
+            // the Laguerre cell is empty (redundant ball): A_i = 0 and no simplex of C holds i
+            if (lane == 0) {
+                A.areas[i] = 0.0;
+                if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = 0.0; }
+            }
+            __syncwarp();
+            continue;
+        }
+
+        // ---------------- Step 2a: tetrahedra of C (cell vertices inside B_i)
+        unsigned kmask = 0;
+#pragma unroll
+        for (int r = 0; r < SPL; ++r) {
+            int t = r * 32 + lane;
+            uint8_t f = 0;
+            if (alive >> r & 1) {
+                uchar4 v = S->tv[t];
+                if (v.x < NG || v.y < NG || v.z < NG) f = 2;
+                else {
+                    FA<R> P;
+                    P.v = V[r][0] * V[r][0] + V[r][1] * V[r][1] + V[r][2] * V[r][2] - wi.v * V[r][3] * V[r][3];
+                    P.a = Va[r][0] * Va[r][0] + Va[r][1] * Va[r][1] + Va[r][2] * Va[r][2] + wi.a * Va[r][3] * Va[r][3];
+                    int sg = fa_sign(P, Gam<R>::g, Gam<R>::tiny);
+                    if (sg == 0) sg = resolve_exact(c, PK_TET, S->pg[v.x], S->pg[v.y], S->pg[v.z], 0, Gam<R>::try64);
+                    f = sg <= 0 ? 1 : 0;
+                    if (f) kmask |= 1u << r;
+                }
+            }
+            S->kf[t] = f;
+            S->tf[t] = 0;
+        }
+        __syncwarp();
+
+        // ---------------- Step 2b: triangles of C (cell edges meeting B_i)
+#pragma unroll
+        for (int r = 0; r < SPL; ++r) {
+            if (!(alive >> r & 1)) continue;
+            int t = r * 32 + lane;
+            uchar4 v = S->tv[t], adj = S->ta[t];
+            for (int k = 0; k < 3; ++k) {
+                int t2 = tv_get(adj, k) & (NT - 1);
+                if (t2 < t) continue;   // each cell edge once (t2 == t impossible)
+                uint8_t a = tv_get(v, k), b = tv_get(v, (k + 1) % 3), cc = tv_get(v, (k + 2) % 3);
+                if (a < NG || b < NG) continue;
+                uchar4 w = S->tv[t2];
+                uint8_t d = (w.x != a && w.x != b) ? w.x : ((w.y != a && w.y != b) ? w.y : w.z);
+                bool inK = S->kf[t] == 1 || S->kf[t2] == 1;
+                if (!inK && psign<PK_TRI>(S, c, wi, a, b) <= 0) {
+                    bool unatt = (cc < NG || psign<PK_TRIB>(S, c, wi, a, b, cc) <= 0) &&
+                                 (d < NG || psign<PK_TRIB>(S, c, wi, a, b, d) <= 0);
+                    inK = unatt;
+                }
+                if (inK) {
+                    uchar4 adj2 = S->ta[t2];
+                    int k2 = adj2.x == t ? 0 : (adj2.y == t ? 1 : 2);
+                    atomicOr(&S->tf[t], (1u << k) | (16u << k));
+                    atomicOr(&S->tf[t2], 1u << k2);
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---------------- Step 2c / 3: faces (edges of C), area terms, gradient gathers
+        // Vectors and angles are evaluated in R (float in the mixed mode); every scalar
+        // combination (normalisation by 2 pi, caps, coefficients, sums) is done in FP64.
+        const R zero = (R)0;
+        const double TWO_PI = 6.283185307179586476925;
+        double area_acc = 0.0;
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        const double wi_w = A.w ? A.w[i] : 1.0;
+        int myEK = 0;
+        for (int a = NG + lane; a < NG + nc; a += 32) {
+            uint8_t flag = 0;
+            double phi_sum = 0.0;
+            int st = S->start[a];
+            bool active = false;
+            if (st != NONE) {
+                uchar4 v = S->tv[st & (NT - 1)];
+                active = v.x == a || v.y == a || v.z == a;
+            }
+            if (active) {
+                int t = st & (NT - 1);
+                int nv = 0, nk = 0;
+                bool ghost = false, triK = false, inside = true;
+                P3<R> gsum = {zero, zero, zero};
+                const P3<R> O = {zero, zero, zero};
+                const P3<R> pa = ppos(S, a);
+                for (int step = 0; step < NT; ++step) {
+                    uchar4 v = S->tv[t];
+                    int k = v.x == a ? 0 : (v.y == a ? 1 : 2);
+                    uint8_t b = tv_get(v, (k + 1) % 3), cc = tv_get(v, (k + 2) % 3);
+                    ++nv;
+                    if (S->kf[t] == 2) ghost = true;
+                    if (S->kf[t] == 1) {
+                        ++nk;
+                        P3<R> pb = ppos(S, b), pc = ppos(S, cc);
+                        phi_sum += (double)dihedral(O, pa, pb, pc);
+                        if (GRAD) {
+                            // (i, a, b, c) is positively oriented: (a, b, c) is counter-clockwise
+                            P3<R> gu, gv, gc, gd;
+                            dihedral_grad_s(O, pa, pb, pc, (R)1, gu, gv, gc, gd);
+                            gsum = gsum + gu;
+                        }
+                    }
+                    if ((S->tf[t] >> k) & 1) triK = true;
+                    int nx = tv_get(S->ta[t], k) & (NT - 1);
+                    t = nx;
+                    if (t == (st & (NT - 1))) break;
+                    if (step == NT - 1) S->bad = 3;
+                }
+                bool closed = (nk == nv) && !ghost;
+                bool eK = triK;
+                if (!eK && psign<PK_EDGE>(S, c, wi, a, 0) <= 0) {
+                    // is the edge orthocentre inside the face polygon?  walk again over its sides
+                    t = st & (NT - 1);
+                    for (int step = 0; step < NT && inside; ++step) {
+                        uchar4 v = S->tv[t];
+                        int k = v.x == a ? 0 : (v.y == a ? 1 : 2);
+                        uint8_t b = tv_get(v, (k + 1) % 3);
+                        if (b >= NG && psign<PK_EDGEB>(S, c, wi, a, b) > 0) inside = false;
+                        t = tv_get(S->ta[t], k) & (NT - 1);
+                        if (t == (st & (NT - 1))) break;
+                    }
+                    eK = inside;
+                }
+                if (eK) {
+                    flag = 1 | (closed ? 2 : 0);
+                    myEK = 1;
+                    if (!closed) {
+                        // edge term of A_i (Eqs. phiedge, edge): - Phi_ia S_ia^(i)
+                        double phi = 1.0 - phi_sum / TWO_PI;
+                        int ga = S->pg[a];
+                        double d = (double)norm3(pa), Ra = A.R[ga];
+                        area_acc -= phi * cap64(d, c.Ri, Ra);
+                        if (GRAD) {
+                            double wa = A.w ? A.w[ga] : 1.0;
+                            double ti = (d * d + c.Ri * c.Ri - Ra * Ra) / (2.0 * d), ta = d - ti;
+                            // vertex + edge parts of the dihedral derivatives around ia (Eq. inexclu)
+                            double kap = -(wi_w * c.Ri * ti + wa * Ra * ta);
+                            // cap derivatives (Eq. edge): -Phi (2 pi / d)(w_i R_i t_a + w_a R_a t_i) u
+                            double cf = -phi * TWO_PI / (d * d) * (wi_w * c.Ri * ta + wa * Ra * ti);
+                            gx += kap * (double)gsum.x + cf * (double)pa.x;
+                            gy += kap * (double)gsum.y + cf * (double)pa.y;
+                            gz += kap * (double)gsum.z + cf * (double)pa.z;
+                        }
+                    }
+                }
+            }
+            S->eflag[a] = flag;
+        }
+        __syncwarp();
+
+        // vertex i in C?  (an edge of C holds it, or p_i lies in its own cell)
+        bool iK = __any_sync(FULL, myEK);
+        bool icl = true;   // cell entirely inside B_i: interior vertex
+#pragma unroll
+        for (int r = 0; r < SPL; ++r)
+            if ((alive >> r & 1) && !(kmask >> r & 1)) icl = false;
+        icl = __all_sync(FULL, icl);
+        if (!iK) {
+            bool ok = true;
+            for (int a = NG + lane; a < NG + nc; a += 32) {
+                int st = S->start[a];
+                if (st == NONE) continue;
+                uchar4 v = S->tv[st & (NT - 1)];
+                if (!(v.x == a || v.y == a || v.z == a)) continue;
+                FA<R> b = {S->pq[a][3], S->pB[a]};
+                int sg = fa_sign(b, Gam<R>::g, Gam<R>::tiny);
+                if (sg == 0) sg = resolve_exact(c, PK_VERT, S->pg[a], 0, 0, 0, Gam<R>::try64);
+                if (sg < 0) ok = false;
+            }
+            iK = __all_sync(FULL, ok);
+        }
+
+        // vertex term Omega_i 4 pi R_i^2 (Eq. vertex), Omega_i = 1 - sum of solid angles / 4 pi
+        if (iK && !icl) {
+            double om = 0.0;
+#pragma unroll
+            for (int r = 0; r < SPL; ++r) {
+                if (!(kmask >> r & 1)) continue;
+                uchar4 v = S->tv[r * 32 + lane];
+                om += (double)solid_angle_half(ppos(S, v.x), ppos(S, v.y), ppos(S, v.z));
+            }
+            om = warp_sum_d(om);
+            if (lane == 0) area_acc += (1.0 - om / TWO_PI) * 2.0 * TWO_PI * c.Ri * c.Ri;
+        }
+
+        // triangle terms: c_iab S_iab^(i) (Eq. trianglev) and the gradient of the triangle
+        // terms of i, a and b (Eq. triangle) and of the dihedral (wing) terms that do not cancel
+#pragma unroll
+        for (int r = 0; r < SPL; ++r) {
+            if (!(alive >> r & 1)) continue;
+            int t = r * 32 + lane;
+            unsigned f = S->tf[t];
+            for (int k = 0; k < 3; ++k) {
+                if (!((f >> (4 + k)) & 1)) continue;   // processed by its canonical owner only
+                uchar4 v = S->tv[t];
+                uint8_t a = tv_get(v, k), b = tv_get(v, (k + 1) % 3), cc = tv_get(v, (k + 2) % 3);
+                int t2 = tv_get(S->ta[t], k) & (NT - 1);
+                int nk = (S->kf[t] == 1) + (S->kf[t2] == 1);
+                if (nk == 2) continue;   // interior triangle: coefficient 0, wing terms cancel
+                double cf = 1.0 - 0.5 * nk;
+                P3<R> pa = ppos(S, a), pb = ppos(S, b);
+                int ga = S->pg[a], gb = S->pg[b];
+                double Ra = A.R[ga], Rb = A.R[gb];
+                area_acc += cf * tri_term_mixed(pa, pb, c.Ri, Ra, Rb);
+                if (GRAD) {
+                    const P3<R> O = {zero, zero, zero};
+                    double wa = A.w ? A.w[ga] : 1.0, wb = A.w ? A.w[gb] : 1.0;
+                    R Raf = (R)Ra, Rbf = (R)Rb;
+                    P3<R> g2, g3;
+                    // owner i: d/dp_i = -(g2 + g3)
+                    lens_grad(pa, pb, Rr, Raf, Rbf, g2, g3);
+                    double sx = -wi_w * (double)(g2.x + g3.x), sy = -wi_w * (double)(g2.y + g3.y),
+                           sz = -wi_w * (double)(g2.z + g3.z);
+                    // owner a: p_i is the second centre
+                    lens_grad(O - pa, pb - pa, Raf, Rr, Rbf, g2, g3);
+                    sx += wa * (double)g2.x; sy += wa * (double)g2.y; sz += wa * (double)g2.z;
+                    // owner b
+                    lens_grad(O - pb, pa - pb, Rbf, Rr, Raf, g2, g3);
+                    sx += wb * (double)g2.x; sy += wb * (double)g2.y; sz += wb * (double)g2.z;
+                    sx *= cf; sy *= cf; sz *= cf;
+                    if (nk == 1) {
+                        // the single tetrahedron of C on this triangle: (i, a, b, x); its
+                        // orientation is + when it is the cell vertex t, - when it is t2
+                        uchar4 w = S->tv[t2];
+                        uint8_t xo = (w.x != a && w.x != b) ? w.x : ((w.y != a && w.y != b) ? w.y : w.z);
+                        bool on_t = S->kf[t] == 1;
+                        uint8_t x = on_t ? cc : xo;
+                        double dab = (double)norm3(pb - pa);
+                        double tab = (dab * dab + Ra * Ra - Rb * Rb) / (2.0 * dab), tba = dab - tab;
+                        double kap = -(wa * Ra * tab + wb * Rb * tba);
+                        P3<R> gu, gv, gc, gd;
+                        dihedral_grad_s(pa, pb, O, ppos(S, x), on_t ? (R)1 : (R)-1, gu, gv, gc, gd);
+                        sx += kap * (double)gc.x; sy += kap * (double)gc.y; sz += kap * (double)gc.z;
+                    }
+                    gx += sx;
+                    gy += sy;
+                    gz += sz;
+                }
+            }
+        }
+
+        area_acc = warp_sum_d(area_acc);
+        if (GRAD) {
+            gx = warp_sum_d(gx);
+            gy = warp_sum_d(gy);
+            gz = warp_sum_d(gz);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            if (S->bad) {
+                atomicOr(A.status, ST_BADCELL);
+                area_acc = __longlong_as_double(0x7ff8000000000000ll);
+            }
+            A.areas[i] = iK ? area_acc : 0.0;
+            if (GRAD && A.grad) {
+                A.grad[3 * i] = iK ? gx : 0.0;
+                A.grad[3 * i + 1] = iK ? gy : 0.0;
+                A.grad[3 * i + 2] = iK ? gz : 0.0;
+            }
+        }
+
+        // ---------------- optional export of the simplices of C containing i
+        if (EXPORT) {
+            auto emit = [&](int v0, int v1, int v2, int v3) {
+                unsigned long long pos = atomicAdd(A.nrec, 1ull);
+                if ((long long)pos < A.max_rec) {
+                    int* rr = A.rec + 5 * pos;
+                    int tmp[4] = {v0, v1, v2, v3};
+                    // sort the atom indices (-1 last)
+                    for (int p = 0; p < 4; ++p)
+                        for (int q2 = p + 1; q2 < 4; ++q2) {
+                            bool sw = (tmp[q2] >= 0) && (tmp[p] < 0 || tmp[q2] < tmp[p]);
+                            if (sw) { int x = tmp[p]; tmp[p] = tmp[q2]; tmp[q2] = x; }
+                        }
+                    rr[0] = i; rr[1] = tmp[0]; rr[2] = tmp[1]; rr[3] = tmp[2]; rr[4] = tmp[3];
+                }
+            };
+            if (lane == 0 && iK) emit(i, -1, -1, -1);
+            for (int a = NG + lane; a < NG + nc; a += 32)
+                if (S->eflag[a] & 1) emit(i, S->pg[a], -1, -1);
+#pragma unroll
+            for (int r = 0; r < SPL; ++r) {
+                if (!(alive >> r & 1)) continue;
+                int t = r * 32 + lane;
+                uchar4 v = S->tv[t];
+                if (kmask >> r & 1) emit(i, S->pg[v.x], S->pg[v.y], S->pg[v.z]);
+                unsigned f = S->tf[t];
+                for (int k = 0; k < 3; ++k)
+                    if ((f >> (4 + k)) & 1) emit(i, S->pg[tv_get(v, k)], S->pg[tv_get(v, (k + 1) % 3)], -1);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+#ifndef DSASA_ATOMS_NO_LAUNCH
+template <class R>
+cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    int blocks = (a.n + WARPS - 1) / WARPS;
+    if (grad && a.rec == nullptr) k_atoms<R, true><<<blocks, WARPS * 32, 0, s>>>(a);
+    else k_atoms<R, false><<<blocks, WARPS * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+#endif
+
+}  // namespace dsasa

@@ -1,0 +1,7 @@
+// All-FP64 instantiation of the per-atom kernel: FP64 terms, FP64 -> exact predicates
+// (see dsasa_atoms.cuh).
+#include "dsasa_atoms.cuh"
+
+namespace dsasa {
+cudaError_t launch_atoms_f64(const AtomArgs& a, bool grad, cudaStream_t s) { return launch_atoms_t<double>(a, grad, s); }
+}  // namespace dsasa

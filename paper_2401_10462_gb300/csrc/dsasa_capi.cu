@@ -1,0 +1,356 @@
+// C ABI of the dSASA library (declared in include/dsasa.h): context, capacity management,
+// argument validation, launches and the device status word.
+#include "../../include/dsasa.h"
+#include "dsasa_kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+using namespace dsasa;
+
+struct dsasa_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    dsasa_config cfg{};
+    // capacities
+    int64_t cap_atoms = 0;
+    int64_t cap_mol = 0;
+    int64_t cap_cells = 0;
+    // scratch
+    double* R = nullptr;
+    float4* f4 = nullptr;
+    int* molid = nullptr;
+    int* rank = nullptr;
+    int* cell = nullptr;
+    int* sidx = nullptr;
+    float4* sf4 = nullptr;
+    unsigned* bbox = nullptr;
+    MolGrid* grids = nullptr;
+    int* counts = nullptr;
+    int* cstart = nullptr;
+    int* blocksums = nullptr;
+    long long* offsets = nullptr;
+    int* status = nullptr;      // [0] status bits, [1] total cells
+    unsigned long long* nrec = nullptr;
+    // staging for the host-buffer entry point
+    int64_t cap_host = 0;
+    double* h_xyz = nullptr;
+    double* h_rad = nullptr;
+    double* h_w = nullptr;
+    double* h_area = nullptr;
+    double* h_grad = nullptr;
+    char err[512] = {0};
+};
+
+namespace {
+
+const char* const kVersion = "dsasa-gb300 0.1 (sm_103a)";
+
+dsasa_status fail(dsasa_ctx* c, dsasa_status st, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        std::vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+dsasa_status cuda_fail(dsasa_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? DSASA_ERR_OOM : DSASA_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+template <class T> void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void free_scratch(dsasa_ctx* c) {
+    dfree(c->R); dfree(c->f4); dfree(c->molid); dfree(c->rank); dfree(c->cell); dfree(c->sidx); dfree(c->sf4);
+    dfree(c->bbox); dfree(c->grids); dfree(c->counts); dfree(c->cstart); dfree(c->blocksums); dfree(c->offsets);
+    c->cap_atoms = c->cap_mol = c->cap_cells = 0;
+}
+void free_host_staging(dsasa_ctx* c) {
+    dfree(c->h_xyz); dfree(c->h_rad); dfree(c->h_w); dfree(c->h_area); dfree(c->h_grad);
+    c->cap_host = 0;
+}
+
+int64_t cells_for(int64_t n, int64_t n_mol) { return 8 * n + 64 * n_mol + 64; }
+
+dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
+    int64_t need_cells = cells_for(n, n_mol);
+    if (n <= c->cap_atoms && n_mol <= c->cap_mol && need_cells <= c->cap_cells) return DSASA_OK;
+    if (c->cfg.max_atoms > 0 && c->cap_atoms > 0)
+        return fail(c, DSASA_ERR_CAPACITY, "n=%lld molecules=%lld exceed the fixed capacity (max_atoms=%lld)",
+                    (long long)n, (long long)n_mol, (long long)c->cfg.max_atoms);
+    if (n > 0x3fffffff || need_cells > 0x7ffffff0)
+        return fail(c, DSASA_ERR_CAPACITY, "n=%lld is beyond the 32-bit index range of this build", (long long)n);
+    // the stream may still use the old buffers
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+    free_scratch(c);
+    int64_t na = n + n / 4 + 256, nm = n_mol + n_mol / 4 + 4;
+    if (c->cfg.max_atoms > 0) { na = std::max<int64_t>(n, c->cfg.max_atoms); nm = std::max<int64_t>(nm, 4096); }
+    int64_t nc = cells_for(na, nm);
+    if (c->cfg.max_cells > 0 && c->cfg.max_cells < nc) nc = std::max<int64_t>(c->cfg.max_cells, 64);
+    int64_t nbs = (int64_t)scan_scratch_ints((int)nc) + 16;
+#define ALLOC(ptr, count)                                                               \
+    e = cudaMalloc((void**)&c->ptr, sizeof(*c->ptr) * (size_t)(count));                 \
+    if (e != cudaSuccess) { free_scratch(c); return cuda_fail(c, e, "cudaMalloc " #ptr); }
+    ALLOC(R, na) ALLOC(f4, na) ALLOC(molid, na) ALLOC(rank, na) ALLOC(cell, na) ALLOC(sidx, na) ALLOC(sf4, na)
+    ALLOC(bbox, 8 * nm) ALLOC(grids, nm) ALLOC(counts, nc + 1) ALLOC(cstart, nc + 1) ALLOC(blocksums, nbs)
+    ALLOC(offsets, nm + 1)
+#undef ALLOC
+    c->cap_atoms = na;
+    c->cap_mol = nm;
+    c->cap_cells = nc;
+    return DSASA_OK;
+}
+
+dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n, int n_mol,
+                 const long long* offsets_dev, const double* w, double* areas, double* grad, int* rec,
+                 int64_t max_rec) {
+    dsasa_status st = ensure(c, n, n_mol);
+    if (st != DSASA_OK) return st;
+    BuildArgs b{};
+    b.xyz = coords;
+    b.radii = radii;
+    b.probe = probe;
+    b.n = (int)n;
+    b.n_mol = n_mol;
+    b.offsets = offsets_dev;
+    b.skin = c->cfg.skin;
+    b.max_cells = (int)c->cap_cells;
+    b.R = c->R; b.f4 = c->f4; b.molid = c->molid; b.rank = c->rank; b.cell = c->cell;
+    b.bbox = c->bbox; b.grids = c->grids; b.counts = c->counts; b.cstart = c->cstart; b.sidx = c->sidx;
+    b.sf4 = c->sf4; b.blocksums = c->blocksums; b.status = c->status; b.ncells_out = c->status + 1;
+    cudaError_t e = launch_build(b, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cell-list launch");
+    AtomArgs a{};
+    a.xyz = coords;
+    a.R = c->R;
+    a.sf4 = c->sf4;
+    a.sidx = c->sidx;
+    a.molid = c->molid;
+    a.cstart = c->cstart;
+    a.grids = c->grids;
+    a.w = w;
+    a.areas = areas;
+    a.grad = grad;
+    a.n = (int)n;
+    a.status = c->status;
+    a.rec = rec;
+    a.max_rec = max_rec;
+    a.nrec = c->nrec;
+    e = c->cfg.precision == DSASA_FP64 ? launch_atoms_f64(a, grad != nullptr, c->stream)
+                                       : launch_atoms_f32(a, grad != nullptr, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "atom kernel launch");
+    return DSASA_OK;
+}
+
+dsasa_status check_common(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
+                          const double* areas) {
+    if (!c) return DSASA_ERR_ARG;
+    if (n < 0) return fail(c, DSASA_ERR_ARG, "n must be >= 0 (got %lld)", (long long)n);
+    if (!std::isfinite(probe) || probe < 0) return fail(c, DSASA_ERR_ARG, "probe must be finite and >= 0");
+    if (n > 0 && (!coords || !radii || !areas)) return fail(c, DSASA_ERR_ARG, "coords, radii and areas_out must be non-NULL");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return DSASA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dsasa_default_config(dsasa_config* cfg) {
+    if (!cfg) return;
+    cfg->precision = DSASA_MIXED;
+    cfg->skin = 0.0;
+    cfg->max_atoms = 0;
+    cfg->max_cells = 0;
+}
+
+const char* dsasa_version(void) { return kVersion; }
+
+dsasa_status dsasa_create(dsasa_ctx** out, int device, void* cuda_stream, const dsasa_config* cfg) {
+    if (!out) return DSASA_ERR_ARG;
+    *out = nullptr;
+    dsasa_ctx* c = new (std::nothrow) dsasa_ctx();
+    if (!c) return DSASA_ERR_OOM;
+    if (cfg) c->cfg = *cfg; else dsasa_default_config(&c->cfg);
+    if ((c->cfg.precision != DSASA_MIXED && c->cfg.precision != DSASA_FP64) || !(c->cfg.skin >= 0.0) ||
+        c->cfg.max_atoms < 0 || c->cfg.max_cells < 0) {
+        delete c;
+        return DSASA_ERR_ARG;
+    }
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->status, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->nrec, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        if (c->status) cudaFree(c->status);
+        if (c->nrec) cudaFree(c->nrec);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? DSASA_ERR_OOM : DSASA_ERR_CUDA;
+    }
+    if (c->cfg.max_atoms > 0) {
+        dsasa_status st = ensure(c, c->cfg.max_atoms, 1);
+        if (st != DSASA_OK) { dsasa_destroy(c); return st; }
+    }
+    *out = c;
+    return DSASA_OK;
+}
+
+dsasa_status dsasa_set_stream(dsasa_ctx* c, void* cuda_stream) {
+    if (!c) return DSASA_ERR_ARG;
+    c->stream = (cudaStream_t)cuda_stream;
+    return DSASA_OK;
+}
+
+dsasa_status dsasa_set_precision(dsasa_ctx* c, int precision) {
+    if (!c) return DSASA_ERR_ARG;
+    if (precision != DSASA_MIXED && precision != DSASA_FP64) return fail(c, DSASA_ERR_ARG, "unknown precision %d", precision);
+    c->cfg.precision = precision;
+    return DSASA_OK;
+}
+
+dsasa_status dsasa_compute_vjp(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
+                               const double* area_weights, double* areas_out, double* grad_out) {
+    dsasa_status st = check_common(c, coords, radii, probe, n, areas_out);
+    if (st != DSASA_OK || n == 0) return st;
+    return run(c, coords, radii, probe, n, 1, nullptr, area_weights, areas_out, grad_out, nullptr, 0);
+}
+
+dsasa_status dsasa_compute(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
+                           double* areas_out, double* grad_out) {
+    return dsasa_compute_vjp(c, coords, radii, probe, n, nullptr, areas_out, grad_out);
+}
+
+dsasa_status dsasa_compute_batch(dsasa_ctx* c, int n_mol, const int64_t* atom_offsets, const double* coords,
+                                 const double* radii, double probe, const double* area_weights, double* areas_out,
+                                 double* grad_out) {
+    if (!c) return DSASA_ERR_ARG;
+    if (n_mol < 0 || (n_mol > 0 && !atom_offsets)) return fail(c, DSASA_ERR_ARG, "invalid molecule offsets");
+    if (n_mol == 0) return DSASA_OK;
+    if (atom_offsets[0] != 0) return fail(c, DSASA_ERR_ARG, "atom_offsets[0] must be 0");
+    for (int m = 0; m < n_mol; ++m)
+        if (atom_offsets[m + 1] < atom_offsets[m]) return fail(c, DSASA_ERR_ARG, "atom_offsets must be non-decreasing");
+    int64_t n = atom_offsets[n_mol];
+    dsasa_status st = check_common(c, coords, radii, probe, n, areas_out);
+    if (st != DSASA_OK || n == 0) return st;
+    st = ensure(c, n, n_mol);
+    if (st != DSASA_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(c->offsets, atom_offsets, sizeof(long long) * (size_t)(n_mol + 1),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "offsets upload");
+    return run(c, coords, radii, probe, n, n_mol, c->offsets, area_weights, areas_out, grad_out, nullptr, 0);
+}
+
+dsasa_status dsasa_compute_host(dsasa_ctx* c, const double* coords_host, const double* radii_host, double probe,
+                                int64_t n, const double* weights_host, double* areas_host, double* grad_host) {
+    dsasa_status st = check_common(c, coords_host, radii_host, probe, n, areas_host);
+    if (st != DSASA_OK || n == 0) return st;
+    cudaError_t e;
+    if (n > c->cap_host) {
+        if (c->cfg.max_atoms > 0 && n > c->cfg.max_atoms)
+            return fail(c, DSASA_ERR_CAPACITY, "n=%lld exceeds max_atoms", (long long)n);
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+        free_host_staging(c);
+        int64_t cap = n + n / 4 + 256;
+#define ALLOC(ptr, count)                                                           \
+    e = cudaMalloc((void**)&c->ptr, sizeof(double) * (size_t)(count));             \
+    if (e != cudaSuccess) { free_host_staging(c); return cuda_fail(c, e, "cudaMalloc " #ptr); }
+        ALLOC(h_xyz, 3 * cap) ALLOC(h_rad, cap) ALLOC(h_w, cap) ALLOC(h_area, cap) ALLOC(h_grad, 3 * cap)
+#undef ALLOC
+        c->cap_host = cap;
+    }
+    e = cudaMemcpyAsync(c->h_xyz, coords_host, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_rad, radii_host, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && weights_host)
+        e = cudaMemcpyAsync(c->h_w, weights_host, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+    st = run(c, c->h_xyz, c->h_rad, probe, n, 1, nullptr, weights_host ? c->h_w : nullptr, c->h_area,
+             grad_host ? c->h_grad : nullptr, nullptr, 0);
+    if (st != DSASA_OK) return st;
+    e = cudaMemcpyAsync(areas_host, c->h_area, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && grad_host)
+        e = cudaMemcpyAsync(grad_host, c->h_grad, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+    return DSASA_OK;
+}
+
+dsasa_status dsasa_status_sync(dsasa_ctx* c) {
+    if (!c) return DSASA_ERR_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    int h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, c->status, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+    int s = h[0];
+    if (s == 0) return DSASA_OK;
+    if (s & ST_INPUT) return fail(c, DSASA_ERR_INPUT, "non-finite coordinate or radius (status 0x%x)", s);
+    if (s & (ST_CAND_OVF | ST_TRI_OVF | ST_GRID_OVF | ST_EXPORT_OVF))
+        return fail(c, DSASA_ERR_CAPACITY, "a fixed per-atom or grid capacity was exceeded (status 0x%x)", s);
+    if (s & (ST_UNRESOLVED | ST_BADCELL))
+        return fail(c, DSASA_ERR_UNRESOLVED, "an exact predicate or a cell could not be resolved (status 0x%x)", s);
+    return fail(c, DSASA_ERR_DEGENERATE, "an exactly degenerate configuration was met (status 0x%x)", s);
+}
+
+dsasa_status dsasa_export_complex(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
+                                  int32_t* records, int64_t max_records, int64_t* n_records) {
+    if (!c || !n_records) return DSASA_ERR_ARG;
+    *n_records = 0;
+    if (!records && max_records > 0) return fail(c, DSASA_ERR_ARG, "records is NULL");
+    // areas are produced as a by-product into the host staging buffer
+    dsasa_status st = check_common(c, coords, radii, probe, n, coords);
+    if (st != DSASA_OK || n == 0) return st;
+    double* areas = nullptr;
+    cudaError_t e = cudaMalloc((void**)&areas, sizeof(double) * (size_t)n);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc export areas");
+    e = cudaMemsetAsync(c->nrec, 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) { cudaFree(areas); return cuda_fail(c, e, "memset"); }
+    st = run(c, coords, radii, probe, n, 1, nullptr, nullptr, areas, nullptr, records ? records : (int32_t*)areas,
+             records ? max_records : 0);
+    unsigned long long cnt = 0;
+    if (st == DSASA_OK) {
+        e = cudaMemcpyAsync(&cnt, c->nrec, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = cuda_fail(c, e, "export count");
+    }
+    cudaFree(areas);
+    if (st != DSASA_OK) return st;
+    *n_records = (int64_t)cnt;
+    if ((int64_t)cnt > max_records) return fail(c, DSASA_ERR_CAPACITY, "%llu records > capacity %lld", cnt, (long long)max_records);
+    return DSASA_OK;
+}
+
+const char* dsasa_last_error(const dsasa_ctx* c) { return c ? c->err : "null context"; }
+
+void dsasa_destroy(dsasa_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    free_scratch(c);
+    free_host_staging(c);
+    if (c->status) cudaFree(c->status);
+    if (c->nrec) cudaFree(c->nrec);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// Cell-list build for the neighbour search (input preparation and binning).
+//
+// Atoms are binned per molecule into cubic cells of edge >= 2 R_max + skin + slack, so every
+// pair of overlapping balls |p_i - p_j| < R_i + R_j lies in the same or adjacent cells.  The
+// binning is a counting sort (atomic counts -> exclusive scan -> scatter); the order inside a
+// cell is not deterministic, which is harmless because each atom later sorts its candidate
+// list by (plane distance, atom index).  The sorted float4 copy (x, y, z, R) gives coalesced
+// neighbour-tile loads in the atom kernel.
+#include "dsasa_kernels.cuh"
+
+#include <math.h>
+
+namespace dsasa {
+
+namespace {
+
+__device__ __forceinline__ unsigned fenc(float f) {
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fdec(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__global__ void k_bbox_init(unsigned* bbox, int n_mol) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_mol) return;
+    unsigned lo = fenc(INFINITY), hi = fenc(-INFINITY);
+    for (int k = 0; k < 3; ++k) { bbox[8 * m + k] = lo; bbox[8 * m + 3 + k] = hi; }
+    bbox[8 * m + 6] = fenc(0.0f);
+    bbox[8 * m + 7] = 0;
+}
+
+__global__ void k_prep(BuildArgs a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int m = 0;
+    if (a.offsets) {
+        int lo = 0, hi = a.n_mol - 1;   // last m with offsets[m] <= i
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (a.offsets[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        m = lo;
+    }
+    double x = a.xyz[3 * i], y = a.xyz[3 * i + 1], z = a.xyz[3 * i + 2];
+    double R = a.radii[i] + a.probe;
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(R)) || !(R > 0.0)) {
+        atomicOr(a.status, ST_INPUT);
+        x = y = z = 0.0;
+        R = 1.0;
+    }
+    a.R[i] = R;
+    a.molid[i] = m;
+    float4 f = make_float4((float)x, (float)y, (float)z, (float)R);
+    a.f4[i] = f;
+    unsigned* bb = a.bbox + 8 * m;
+    atomicMin(bb + 0, fenc(f.x));
+    atomicMin(bb + 1, fenc(f.y));
+    atomicMin(bb + 2, fenc(f.z));
+    atomicMax(bb + 3, fenc(f.x));
+    atomicMax(bb + 4, fenc(f.y));
+    atomicMax(bb + 5, fenc(f.z));
+    atomicMax(bb + 6, fenc(f.w));
+}
+
+// per molecule: cell size and dimensions (cell count stored in base for the scan below)
+__global__ void k_grid_local(BuildArgs a) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.n_mol) return;
+    const unsigned* bb = a.bbox + 8 * m;
+    MolGrid g;
+    long long nm = a.offsets ? (a.offsets[m + 1] - a.offsets[m]) : a.n;
+    if (nm <= 0) {
+        for (int k = 0; k < 3; ++k) { g.lo[k] = 0.f; g.dims[k] = 1; }
+        g.inv_cell = 1.f;
+        g.margin = 0.f;
+        g.rmax = 0.f;
+        g.base = 1;
+        a.grids[m] = g;
+        return;
+    }
+    float lo[3], hi[3], amax = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = fdec(bb[k]);
+        hi[k] = fdec(bb[3 + k]);
+        amax = fmaxf(amax, fmaxf(fabsf(lo[k]), fabsf(hi[k])));
+    }
+    float rmax = fdec(bb[6]);
+    // float rounding of coordinates (|x| 2^-24 each), of the difference and of R: slack
+    float margin = 1e-5f + 4.0e-7f * (amax + 16.0f);
+    float cell = 2.0f * rmax + (float)a.skin + 2.0f * margin + 1e-3f;
+    double cap = 8.0 * (double)nm + 64.0;
+    int dims[3];
+    for (int it = 0; it < 64; ++it) {
+        double prod = 1.0;
+        for (int k = 0; k < 3; ++k) {
+            dims[k] = (int)fminf((hi[k] - lo[k]) / cell, 1e6f) + 1;
+            prod *= dims[k];
+        }
+        if (prod <= cap) break;
+        cell *= (float)fmax(1.01, cbrt(prod / cap) * 1.01);
+    }
+    for (int k = 0; k < 3; ++k) { g.lo[k] = lo[k]; g.dims[k] = dims[k]; }
+    g.inv_cell = 1.0f / cell;
+    g.margin = margin + 0.5f * (float)a.skin;
+    g.rmax = rmax;
+    g.base = dims[0] * dims[1] * dims[2];
+    a.grids[m] = g;
+}
+
+// exclusive scan of the per-molecule cell counts (one block)
+__global__ void k_grid_scan(BuildArgs a) {
+    __shared__ int carry;
+    __shared__ int ws[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < a.n_mol; b0 += blockDim.x) {
+        int m = b0 + threadIdx.x;
+        int v = m < a.n_mol ? a.grids[m].base : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (threadIdx.x >= o) s += y;
+            }
+            ws[threadIdx.x] = s;
+        }
+        __syncthreads();
+        int wpre = (threadIdx.x >= 32) ? ws[(threadIdx.x >> 5) - 1] : 0;
+        int excl = carry + wpre + x - v;
+        if (m < a.n_mol) a.grids[m].base = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *a.ncells_out = carry;
+        if (carry > a.max_cells) atomicOr(a.status, ST_GRID_OVF);
+    }
+}
+
+__device__ __forceinline__ int cell_of(const MolGrid& g, float4 f) {
+    int cx = min(max((int)floorf((f.x - g.lo[0]) * g.inv_cell), 0), g.dims[0] - 1);
+    int cy = min(max((int)floorf((f.y - g.lo[1]) * g.inv_cell), 0), g.dims[1] - 1);
+    int cz = min(max((int)floorf((f.z - g.lo[2]) * g.inv_cell), 0), g.dims[2] - 1);
+    return g.base + (cz * g.dims[1] + cy) * g.dims[0] + cx;
+}
+
+__global__ void k_count(BuildArgs a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const MolGrid g = a.grids[a.molid[i]];
+    int c = cell_of(g, a.f4[i]);
+    if (c >= a.max_cells) c = a.max_cells - 1;   // only after a reported overflow
+    a.cell[i] = c;
+    a.rank[i] = atomicAdd(&a.counts[c], 1);
+}
+
+// ---- exclusive scan of counts[0..len) into cstart (3 phases, tile = 256 threads x 16)
+constexpr int SCAN_T = 256, SCAN_V = 16, SCAN_TILE = SCAN_T * SCAN_V;
+
+__device__ int block_excl_scan(int v, int* total) {
+    __shared__ int ws[SCAN_T / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < SCAN_T / 32 ? ws[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < SCAN_T / 32) ws[lane] = s;
+    }
+    __syncthreads();
+    int pre = (w > 0 ? ws[w - 1] : 0) + x - v;
+    *total = ws[SCAN_T / 32 - 1];
+    __syncthreads();
+    return pre;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const int* in, int len, int* bsum) {
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_V;
+    int s = 0;
+    for (int k = 0; k < SCAN_V; ++k) s += (base + k < len) ? in[base + k] : 0;
+    int tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+__global__ void __launch_bounds__(SCAN_T) k_scan_top(int* bsum, int nb) {
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += SCAN_T) {
+        int v = (b0 + threadIdx.x < nb) ? bsum[b0 + threadIdx.x] : 0;
+        int tot;
+        int pre = block_excl_scan(v, &tot);
+        if (b0 + threadIdx.x < nb) bsum[b0 + threadIdx.x] = carry + pre;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+}
+__global__ void __launch_bounds__(SCAN_T) k_scan_down(const int* in, int len, const int* bsum, int* out) {
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_V;
+    int v[SCAN_V];
+    int s = 0;
+    for (int k = 0; k < SCAN_V; ++k) { v[k] = (base + k < len) ? in[base + k] : 0; s += v[k]; }
+    int tot;
+    int pre = block_excl_scan(s, &tot) + bsum[blockIdx.x];
+    for (int k = 0; k < SCAN_V; ++k) {
+        if (base + k <= len) out[base + k] = pre;   // out has len + 1 entries
+        pre += v[k];
+    }
+}
+
+__global__ void k_scatter(BuildArgs a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int pos = a.cstart[a.cell[i]] + a.rank[i];
+    a.sidx[pos] = i;
+    a.sf4[pos] = a.f4[i];
+}
+
+}  // namespace
+
+size_t scan_scratch_ints(int max_cells) { return (size_t)(max_cells + 1 + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+cudaError_t launch_build(const BuildArgs& a, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const int T = 256;
+    int nb = (a.n + T - 1) / T;
+    k_bbox_init<<<(a.n_mol + T - 1) / T, T, 0, s>>>(a.bbox, a.n_mol);
+    k_prep<<<nb, T, 0, s>>>(a);
+    k_grid_local<<<(a.n_mol + T - 1) / T, T, 0, s>>>(a);
+    k_grid_scan<<<1, 1024, 0, s>>>(a);
+    cudaMemsetAsync(a.counts, 0, sizeof(int) * (size_t)(a.max_cells + 1), s);
+    k_count<<<nb, T, 0, s>>>(a);
+    int len = a.max_cells;   // scan the whole capacity: cells past the used range are zero
+    int nt = (len + 1 + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_reduce<<<nt, SCAN_T, 0, s>>>(a.counts, len, a.blocksums);
+    k_scan_top<<<1, SCAN_T, 0, s>>>(a.blocksums, nt);
+    k_scan_down<<<nt, SCAN_T, 0, s>>>(a.counts, len, a.blocksums, a.cstart);
+    k_scatter<<<nb, T, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace dsasa

@@ -1,0 +1,81 @@
+// Shared declarations of the dSASA CUDA kernels (host side and device side).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dsasa {
+
+// device status bits (ORed by kernels, read by dsasa_status_sync)
+enum : int {
+    ST_CAND_OVF = 1,      // more overlapping neighbours than one warp's candidate table holds
+    ST_TRI_OVF = 2,       // cell needed more vertex slots than available
+    ST_UNRESOLVED = 4,    // exact expansion capacity exceeded
+    ST_DEGENERATE = 8,    // an exact tie (zero predicate) was met
+    ST_BADCELL = 16,      // inconsistent cell structure detected (atom output set to NaN)
+    ST_INPUT = 32,        // non-finite input
+    ST_EXPORT_OVF = 64,   // complex export buffer too small
+    ST_GRID_OVF = 128     // cell grid larger than its capacity
+};
+
+// cell grid of one molecule: cells of edge `cell` starting at `lo`, cell id = base + local
+struct MolGrid {
+    float lo[3];
+    float inv_cell;
+    int dims[3];
+    int base;         // first global cell of this molecule
+    float margin;     // conservative slack of the FP32 neighbour test (A)
+    float rmax;       // largest probe-inflated radius of the molecule
+    int pad[2];
+};
+
+struct BuildArgs {
+    const double* xyz;
+    const double* radii;
+    double probe;
+    int n;
+    int n_mol;
+    const long long* offsets;   // device, n_mol + 1 (NULL: one molecule)
+    double skin;
+    int max_cells;
+    // outputs / scratch
+    double* R;         // n
+    float4* f4;        // n  (x, y, z, R) float
+    int* molid;        // n
+    int* rank;         // n
+    int* cell;         // n
+    unsigned* bbox;    // n_mol * 8 (ordered-int encoded: min xyz, max xyz, rmax, pad)
+    MolGrid* grids;    // n_mol
+    int* counts;       // max_cells + 1
+    int* cstart;       // max_cells + 1
+    int* sidx;         // n
+    float4* sf4;       // n
+    int* blocksums;    // scan scratch
+    int* status;
+    int* ncells_out;   // device int: total cells used
+};
+
+struct AtomArgs {
+    const double* xyz;
+    const double* R;
+    const float4* sf4;
+    const int* sidx;
+    const int* molid;
+    const int* cstart;
+    const MolGrid* grids;
+    const double* w;        // NULL = ones
+    double* areas;
+    double* grad;           // NULL = no gradient
+    int n;
+    int* status;
+    // complex export (NULL = off): records {i, v0, v1, v2, v3}
+    int* rec;
+    long long max_rec;
+    unsigned long long* nrec;
+};
+
+cudaError_t launch_build(const BuildArgs& a, cudaStream_t s);
+cudaError_t launch_atoms_f32(const AtomArgs& a, bool grad, cudaStream_t s);
+cudaError_t launch_atoms_f64(const AtomArgs& a, bool grad, cudaStream_t s);
+size_t scan_scratch_ints(int max_cells);
+
+}  // namespace dsasa
