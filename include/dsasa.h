@@ -123,6 +123,30 @@ dsasa_status dsasa_status_sync(dsasa_ctx* ctx);
 dsasa_status dsasa_export_complex(dsasa_ctx* ctx, const double* coords, const double* radii, double probe,
                                   int64_t n, int32_t* records, int64_t max_records, int64_t* n_records);
 
+/* Largest n that dsasa_compute_noalloc accepts. */
+#define DSASA_NOALLOC_MAX_ATOMS 32768
+
+/* dsasa_compute without any device allocation, for callers that must not have a library call
+ * cudaMalloc or cudaFree: for example an application that provisions a fixed device-memory
+ * budget up front, or code whose device memory belongs to another framework's pool.  (The
+ * paper has no counterpart to this entry point; it concerns memory ownership only.)
+ *   - Same inputs and outputs as dsasa_compute (device pointers, caller-owned; grad_out may be
+ *     NULL), computed in the DSASA_MIXED precision on `cuda_stream` (a cudaStream_t or NULL)
+ *     of the current device; no context is involved.
+ *   - Its scratch is one static device array of about 3.8 MB, sized for at most
+ *     DSASA_NOALLOC_MAX_ATOMS atoms and reserved on every GPU that loads the library until
+ *     the process exits.  n > DSASA_NOALLOC_MAX_ATOMS returns DSASA_ERR_CAPACITY and enqueues
+ *     nothing; n = 0 returns DSASA_OK.
+ *   - The first call on a device performs a one-time set-up (it looks up the device address
+ *     of that array); make this first call before any stream capture begins.
+ *   - Every call shares the one array, which keeps the previous call's contents: calls that
+ *     overlap on the GPU (other streams, other host threads) race.  Serialise them.
+ *   - Blocking: the call synchronises `cuda_stream` and returns the device status of this
+ *     call (DSASA_OK, DSASA_ERR_INPUT, DSASA_ERR_CAPACITY, DSASA_ERR_UNRESOLVED or
+ *     DSASA_ERR_DEGENERATE with the meanings above); argument errors return DSASA_ERR_ARG. */
+dsasa_status dsasa_compute_noalloc(const double* coords, const double* radii, double probe, int64_t n,
+                                   double* areas_out, double* grad_out, void* cuda_stream);
+
 /* Message describing the last error of this context ("" if none). */
 const char* dsasa_last_error(const dsasa_ctx* ctx);
 
