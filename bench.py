@@ -255,6 +255,8 @@ def run_gpu(args):
         "gpu_launches": 10 * args.steps,
         "clocks": clk.summary(),
     }
+    if rank == 0 and ws == 1 and not args.no_serving:
+        line["serving"] = serving_measure(512, 12, loads=(0.8,))
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(m)
     if rank == 0:
@@ -309,18 +311,111 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def serving_measure(count: int, pool: int, loads=(0.8,), seed: int = 0, slots: int = 3):
+    """configs[3]: log-uniform 300-50,000-atom requests (70 % globules, 30 % RNA), Poisson
+    arrivals.  The saturated throughput mu is measured first (all requests queued at t = 0);
+    then the stream is replayed at lambda = load x mu and p50 / p99 latency (arrival to
+    result on the host) are reported."""
+    from paper_2401_10462_gb300 import serve, inputs
+    reqs, mols = serve.request_pool(count, seed=seed, pool=pool)
+    srv = serve.Server(slots=slots, slot_atoms=200_000)
+    srv.run(reqs[: min(len(reqs), 32)], realtime=False)          # warm-up
+    for r in reqs:
+        r.done = None
+    sat = srv.run(reqs, realtime=False)
+    mu = sat["requests_per_s"]
+    out = {"requests": count, "pool_molecules": pool, "slots": slots, "saturated_requests_per_s": mu,
+           "saturated_atoms_per_s": sat["atoms_per_s"], "loads": []}
+    for ld in loads:
+        t = inputs.poisson_arrivals(count, ld * mu, seed=seed + 11)
+        for r, ti in zip(reqs, t):
+            r.arrival = float(ti)
+            r.done = None
+        st = srv.run(reqs, realtime=True)
+        out["loads"].append({"lambda_over_mu": ld, "lambda_requests_per_s": ld * mu, "p50_ms": st["p50_ms"],
+                             "p99_ms": st["p99_ms"], "atoms_per_s": st["atoms_per_s"]})
+    srv.close()
+    return out
+
+
+def run_capsid(args):
+    """configs[4]: the 1,000,000-atom capsid-like shell, mixed vs FP64, SASA + gradient."""
+    import torch
+    from paper_2401_10462_gb300 import api, inputs
+    m = inputs.make("shell", 1_000_000, 0)
+    dev = torch.device("cuda", 0)
+    xyz = torch.as_tensor(m.coords, device=dev)
+    rad = torch.as_tensor(m.radii, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    res = {}
+    for prec, steps in (("mixed", args.steps), ("fp64", max(1, args.steps // 2))):
+        ctx = api.Context(stream=stream, precision=prec)
+        a = torch.empty(m.n, dtype=torch.float64, device=dev)
+        g = torch.empty((m.n, 3), dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                ctx.compute(xyz, rad, a, g)
+            ctx.status_sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.compute(xyz, rad, a, g)
+            e1.record(stream)
+            ctx.status_sync()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[prec] = {"ms_per_step": ms, "atoms_per_s": m.n / ms * 1e3, "total_sasa": float(a.sum().item())}
+        ctx.close()
+    print(json.dumps({"workload": "capsid shell 1,000,000 atoms (configs[4])", "outer_radius_A": m.extent,
+                      "density_per_A3": m.density(), "inputs_larger_than_L2": True, **res,
+                      "mixed_over_fp64": res["mixed"]["atoms_per_s"] / res["fp64"]["atoms_per_s"]}), flush=True)
+
+
+def run_trajectory(args):
+    """configs[2]: 20,000-atom globule, E_np through the autograd Function, Gaussian steps
+    (sigma 0.01 A) replayed from one captured CUDA graph; reports ms per graphed step."""
+    import torch
+    from paper_2401_10462_gb300 import autograd as ag, inputs
+    m = inputs.make("globule", 20000, 0)
+    dev = torch.device("cuda", 0)
+    tr = ag.GraphedTrajectory(torch.as_tensor(m.coords, device=dev), torch.as_tensor(m.radii, device=dev),
+                              sigma=0.01, seed=0).capture()
+    tr.replay(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(args.steps, 100)
+    e0.record()
+    tr.replay(steps)      # replays on the trajectory stream, joined back to the current one
+    e1.record()
+    torch.cuda.synchronize()
+    tr.check()
+    ms = e0.elapsed_time(e1) / steps
+    print(json.dumps({"workload": "graphed trajectory, 20,000-atom globule (configs[2])", "steps": steps,
+                      "ms_per_step": ms, "atoms_per_s": m.n / ms * 1e3, "energy_kcal_mol": tr.energy.item()}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="globule5k", choices=["globule5k", "capsid", "trajectory", "serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "capsid":
+        run_capsid(args)
+    elif args.workload == "trajectory":
+        run_trajectory(args)
+    elif args.workload == "serving":
+        print(json.dumps({"workload": "serving stream (configs[3])",
+                          **serving_measure(4096, 32, loads=(0.5, 0.8, 0.95))}), flush=True)
     else:
         run_gpu(args)
 

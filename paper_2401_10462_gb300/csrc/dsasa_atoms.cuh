@@ -31,15 +31,17 @@ namespace dsasa {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int NE = 128;          // plane entries: 0..5 ghosts, 6.. candidates
-constexpr int NG = 6;
-constexpr int KMAX = NE - NG;    // overlapping neighbours per atom
-constexpr int NT = 128;          // cell-vertex slots (4 per lane)
-constexpr int SPL = NT / 32;
+constexpr int NG = 6;            // ghost planes (the initial cube)
 constexpr uint8_t NONE = 0xff;
 constexpr int WARPS = 4;         // warps per block
 
-template <class R> struct Smem {
+// Per-warp cell storage.  NE plane entries (0..5 ghosts, then the candidates in sorted
+// order), NT cell-vertex slots (NT / 32 per lane).  Two capacities are compiled: 64 / 64
+// holds every atom of the molecular workloads measured (at most 58 overlapping neighbours,
+// 54 vertex slots); atoms that do not fit are deferred to a 128 / 128 pass.
+template <class R, int NE, int NT> struct Smem {
+    using Real = R;
+    static constexpr int kNE = NE, kNT = NT;
     R pq[NE][4];          // plane q.x, q.y, q.z, b (relative to p_i)
     R pB[NE];             // magnitude proxy of b for the filters
     int pg[NE];           // global atom index (>= 0) or -1 - ghost id
@@ -53,6 +55,7 @@ template <class R> struct Smem {
     uint8_t kf[NT];       // 0 not in C, 1 tetrahedron of C, 2 involves a ghost plane
     unsigned tf[NT];      // bit k: the triangle of edge k is in C; bit 4+k: it is processed here
     unsigned skey[NE];    // orderable sort key of each candidate
+    uint16_t tl[NT * 3 / 2 + 2];   // compacted exterior triangles (slot << 2 | edge)
     uint8_t rem[NT];
     uint8_t rsl[NT];      // removed slots in order
     uint8_t fs[NT];       // free slot stack
@@ -73,8 +76,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 __device__ __forceinline__ uint8_t tv_get(const uchar4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
-__device__ __forceinline__ void ta_set(Smem<float>* S, int t, int k, uint8_t s) { ((uint8_t*)&S->ta[t & (NT - 1)])[k] = s; }
-__device__ __forceinline__ void ta_set(Smem<double>* S, int t, int k, uint8_t s) { ((uint8_t*)&S->ta[t & (NT - 1)])[k] = s; }
+template <class SM> __device__ __forceinline__ void ta_set(SM* S, int t, int k, uint8_t s) {
+    ((uint8_t*)&S->ta[t & (SM::kNT - 1)])[k] = s;
+}
 
 // ------------------------------------------------------------------ global plane access
 struct Ctx {
@@ -154,8 +158,8 @@ __device__ __noinline__ int resolve_exact(const Ctx& c, int kind, int g0, int g1
 }
 
 // filter planes from the shared table
-template <class R> __device__ __forceinline__ PlaneN<FA<R>> fplane(const Smem<R>* S, int e) {
-    e &= NE - 1;
+template <class SM, class R = typename SM::Real> __device__ __forceinline__ PlaneN<FA<R>> fplane(const SM* S, int e) {
+    e &= SM::kNE - 1;
     PlaneN<FA<R>> P;
     P.q = {{S->pq[e][0], fabs(S->pq[e][0])}, {S->pq[e][1], fabs(S->pq[e][1])}, {S->pq[e][2], fabs(S->pq[e][2])}};
     P.b = {S->pq[e][3], S->pB[e]};
@@ -182,32 +186,39 @@ template <int KIND, class N> __device__ __forceinline__ N eval_k(const PlaneN<N>
 }
 
 // sign of predicate KIND on shared-table planes e0..e3 (FP32/FP64 filter, then slow path)
-template <int KIND, class R> __device__ int psign(const Smem<R>* S, const Ctx& c, const FA<R>& wi, int e0, int e1, int e2 = 0, int e3 = 0) {
+template <int KIND, class SM, class R = typename SM::Real>
+__device__ int psign(const SM* S, const Ctx& c, const FA<R>& wi, int e0, int e1, int e2 = 0, int e3 = 0) {
     PlaneN<FA<R>> P[4] = {fplane(S, e0), fplane(S, e1), fplane(S, e2), fplane(S, e3)};
     int s = fa_sign(eval_k<KIND>(P, wi), Gam<R>::g, Gam<R>::tiny);
     if (s != 0) return s;
     const int kind = KIND;
-    return resolve_exact(c, kind, S->pg[e0 & (NE - 1)], S->pg[e1 & (NE - 1)], S->pg[e2 & (NE - 1)],
-                         S->pg[e3 & (NE - 1)], Gam<R>::try64);
+    constexpr int M = SM::kNE - 1;
+    return resolve_exact(c, kind, S->pg[e0 & M], S->pg[e1 & M], S->pg[e2 & M], S->pg[e3 & M], Gam<R>::try64);
 }
 
-template <class R> __device__ __forceinline__ P3<R> ppos(const Smem<R>* S, int e) {
-    e &= NE - 1;
+template <class SM, class R = typename SM::Real> __device__ __forceinline__ P3<R> ppos(const SM* S, int e) {
+    e &= SM::kNE - 1;
     return {S->pq[e][0], S->pq[e][1], S->pq[e][2]};
 }
 
 // ------------------------------------------------------------------ the kernel
-template <class R, bool GRAD>
-__global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
+template <class R, bool GRAD, int NE, int NT>
+__global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
+    constexpr int SPL = NT / 32;      // vertex slots per lane
+    constexpr int KMAX = NE - NG;     // overlapping neighbours per atom
     const bool EXPORT = A.rec != nullptr;
-    __shared__ Smem<R> smem_all[WARPS];
+    // the large-capacity pass works on the atoms the fast pass deferred
+    const bool deferred = A.work_list != nullptr;
+    const bool can_defer = A.defer_list != nullptr;
+    __shared__ Smem<R, NE, NT> smem_all[WARPS];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    Smem<R>* S = &smem_all[wib];
+    Smem<R, NE, NT>* S = &smem_all[wib];
     const int nwarps = gridDim.x * WARPS;
-    const R PI = pi_t<R>();
+    const int total = deferred ? *A.work_count : A.n;
 
-    for (int s = blockIdx.x * WARPS + wib; s < A.n; s += nwarps) {
+    for (int s0 = blockIdx.x * WARPS + wib; s0 < total; s0 += nwarps) {
+        const int s = deferred ? A.work_list[s0] : s0;
         const int i = A.sidx[s];
         const float4 fi = A.sf4[s];
         const MolGrid G = A.grids[A.molid[i]];
@@ -258,6 +269,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
                 }
             }
         }
+        if (nc > KMAX && can_defer) {
+            if (lane == 0) A.defer_list[atomicAdd(A.defer_count, 1)] = s;
+            __syncwarp();
+            continue;
+        }
         if (nc > KMAX) {
             if (lane == 0) {
                 atomicOr(A.status, ST_CAND_OVF);
@@ -285,7 +301,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
             S->start[e] = NONE;
             if (e >= NG) {
                 // sort key: signed distance of the bisector from p_i (ties: atom index)
-                float kf = (float)(b / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + 1e-300));
+                float qx = (float)q[0], qy = (float)q[1], qz = (float)q[2];
+                float kf = (float)b * rsqrtf(qx * qx + qy * qy + qz * qz + 1e-30f);
                 unsigned u = __float_as_uint(kf);
                 S->skey[e] = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
             }
@@ -300,15 +317,19 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
             }
         }
         __syncwarp();
-        // bitonic sort of 128 (key, payload) pairs, element e = r*32 + lane
-        for (int k = 2; k <= NT; k <<= 1) {
+        // bitonic sort of the first ns (key, payload) pairs, element e = r*32 + lane; the
+        // padding keys are the largest, so sorting a power-of-two prefix that holds all nc
+        // candidates sorts them all
+        const int ns = nc <= 32 ? 32 : (nc <= 64 ? 64 : NT);
+        const int nsr = ns >> 5;
+        for (int k = 2; k <= ns; k <<= 1) {
             for (int j = k >> 1; j > 0; j >>= 1) {
                 if (j >= 32) {
                     int jr = j >> 5;
 #pragma unroll
                     for (int r = 0; r < SPL; ++r) {
                         int r2 = r ^ jr;
-                        if (r2 > r) {
+                        if (r2 > r && r2 < nsr) {
                             int e = r * 32 + lane;
                             bool up = (e & k) == 0;
                             bool sw = up ? (key[r] > key[r2]) : (key[r] < key[r2]);
@@ -321,6 +342,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
                 } else {
 #pragma unroll
                     for (int r = 0; r < SPL; ++r) {
+                        if (r >= nsr) break;
                         int e = r * 32 + lane;
                         unsigned long long ok = __shfl_xor_sync(FULL, key[r], j);
                         unsigned op = __shfl_xor_sync(FULL, pay[r], j);
@@ -412,12 +434,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
 
         // ---------------- clipping by the sorted neighbour planes
         bool empty = false;
+        int nalive = 8;      // live cell vertices (warp-uniform)
+        int nrounds = 1;     // vertex-slot rounds in use: slots < 32 * nrounds (warp-uniform)
         for (int kk = 0; kk < nc && !empty; ++kk) {
             const int m = S->ord[kk] & (NE - 1);
             const PlaneN<FA<R>> M = fplane(S, m);
             unsigned remv = 0;
 #pragma unroll
             for (int r = 0; r < SPL; ++r) {
+                if (r >= nrounds) break;
                 if (!(alive >> r & 1)) continue;
                 FA<R> sv;
                 sv.v = M.q.x.v * V[r][0] + M.q.y.v * V[r][1] + M.q.z.v * V[r][2] - M.b.v * V[r][3];
@@ -431,12 +456,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
                 if (sg > 0) remv |= 1u << r;
             }
             unsigned bal[SPL];
-            int nrem = 0, nalive = 0;
+            int nrem = 0;
 #pragma unroll
             for (int r = 0; r < SPL; ++r) {
-                bal[r] = __ballot_sync(FULL, remv >> r & 1);
+                bal[r] = r < nrounds ? __ballot_sync(FULL, remv >> r & 1) : 0u;
                 nrem += __popc(bal[r]);
-                nalive += __popc(__ballot_sync(FULL, alive >> r & 1));
             }
             if (nrem == 0) continue;
             if (nrem == nalive) { empty = true; break; }
@@ -444,9 +468,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
             int before = 0;
 #pragma unroll
             for (int r = 0; r < SPL; ++r) {
+                if (r >= nrounds) break;
                 int t = r * 32 + lane;
-                S->rem[t] = (remv >> r) & 1;
-                if (remv >> r & 1) S->rsl[before + __popc(bal[r] & lanemask_lt())] = (uint8_t)t;
+                if (remv >> r & 1) {
+                    S->rem[t] = 1;
+                    S->rsl[before + __popc(bal[r] & lanemask_lt())] = (uint8_t)t;
+                }
                 before += __popc(bal[r]);
             }
             __syncwarp();
@@ -456,6 +483,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
             int mynb = 0;
 #pragma unroll
             for (int r = 0; r < SPL; ++r) {
+                if (r >= nrounds) break;
                 if (!(remv >> r & 1)) continue;
                 int t = r * 32 + lane;
                 uchar4 v = S->tv[t], adj = S->ta[t];
@@ -472,13 +500,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
                     if (mynb < 12) myb[mynb++] = a; else S->bad = 1;
                 }
             }
-            int nb = warp_sum_i(mynb);
-            int off = mynb;
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(FULL, off, o);
-                if (lane >= o) off += y;
+            // count and exclusive prefix of the boundary edges by ballots (<= 3 per slot)
+            int nb = 0, off = 0;
+#pragma unroll
+            for (int j = 0; j < 3 * SPL; ++j) {
+                if (j >= 3 * nrounds) break;
+                unsigned bj = __ballot_sync(FULL, mynb > j);
+                nb += __popc(bj);
+                off += __popc(bj & lanemask_lt());
             }
-            off -= mynb;
             const int hw = S->hw, nfree = S->nfree;
             const int extra = nb - nrem;
             if (hw + max(0, extra - nfree) > NT) {
@@ -519,24 +549,32 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
                     S->fs[nfree + y] = (uint8_t)sl;
                 }
             }
-            __syncwarp();
+            const int hw2 = extra <= nfree ? hw : hw + (extra - nfree);
             if (lane == 0) {
                 if (extra <= nfree) S->nfree = nfree - extra;
-                else { S->nfree = 0; S->hw = hw + (extra - nfree); }
+                else { S->nfree = 0; S->hw = hw2; }
             }
+            nalive += extra;
+            nrounds = (hw2 + 31) >> 5;
             __syncwarp();
 #pragma unroll
             for (int r = 0; r < SPL; ++r) {
+                if (r >= nrounds) break;
                 int t = r * 32 + lane;
                 uint8_t st = S->rem[t];
                 if (st == 2) { compute_vertex(r, t); alive |= 1u << r; }
                 else if (st == 1) alive &= ~(1u << r);
-                S->rem[t] = 0;
+                if (st) S->rem[t] = 0;
             }
             __syncwarp();
         }
         __syncwarp();
         const bool bad = S->bad != 0;
+        if (bad && S->bad == 2 && can_defer) {
+            if (lane == 0) A.defer_list[atomicAdd(A.defer_count, 1)] = s;
+            __syncwarp();
+            continue;
+        }
         if (bad) {
             if (lane == 0) {
                 atomicOr(A.status, S->bad == 2 ? ST_TRI_OVF : ST_BADCELL);
@@ -560,6 +598,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
         unsigned kmask = 0;
 #pragma unroll
         for (int r = 0; r < SPL; ++r) {
+            if (r >= nrounds) break;
             int t = r * 32 + lane;
             uint8_t f = 0;
             if (alive >> r & 1) {
@@ -583,6 +622,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
         // ---------------- Step 2b: triangles of C (cell edges meeting B_i)
 #pragma unroll
         for (int r = 0; r < SPL; ++r) {
+            if (r >= nrounds) break;
             if (!(alive >> r & 1)) continue;
             int t = r * 32 + lane;
             uchar4 v = S->tv[t], adj = S->ta[t];
@@ -735,19 +775,34 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
         }
 
         // triangle terms: c_iab S_iab^(i) (Eq. trianglev) and the gradient of the triangle
-        // terms of i, a and b (Eq. triangle) and of the dihedral (wing) terms that do not cancel
+        // terms of i, a and b (Eq. triangle) and of the dihedral (wing) terms that do not
+        // cancel.  The exterior triangles are first compacted into a list so that the lanes
+        // share the work evenly.
+        int ntl = 0;
 #pragma unroll
         for (int r = 0; r < SPL; ++r) {
-            if (!(alive >> r & 1)) continue;
+            if (r >= nrounds) break;
             int t = r * 32 + lane;
-            unsigned f = S->tf[t];
+            unsigned f = (alive >> r & 1) ? S->tf[t] : 0u;
             for (int k = 0; k < 3; ++k) {
-                if (!((f >> (4 + k)) & 1)) continue;   // processed by its canonical owner only
+                bool want = (f >> (4 + k)) & 1;   // processed by its canonical owner only
+                if (want) {
+                    int t2 = tv_get(S->ta[t], k) & (NT - 1);
+                    want = !(S->kf[t] == 1 && S->kf[t2] == 1);   // interior: coefficient 0
+                }
+                unsigned bl = __ballot_sync(FULL, want);
+                if (want) S->tl[ntl + __popc(bl & lanemask_lt())] = (uint16_t)((t << 2) | k);
+                ntl += __popc(bl);
+            }
+        }
+        __syncwarp();
+        for (int e = lane; e < ntl; e += 32) {
+            {
+                const int t = S->tl[e] >> 2, k = S->tl[e] & 3;
                 uchar4 v = S->tv[t];
                 uint8_t a = tv_get(v, k), b = tv_get(v, (k + 1) % 3), cc = tv_get(v, (k + 2) % 3);
                 int t2 = tv_get(S->ta[t], k) & (NT - 1);
                 int nk = (S->kf[t] == 1) + (S->kf[t2] == 1);
-                if (nk == 2) continue;   // interior triangle: coefficient 0, wing terms cancel
                 double cf = 1.0 - 0.5 * nk;
                 P3<R> pa = ppos(S, a), pb = ppos(S, b);
                 int ga = S->pg[a], gb = S->pg[b];
@@ -847,15 +902,31 @@ __global__ void __launch_bounds__(WARPS * 32) k_atoms(AtomArgs A) {
 }  // namespace
 
 #ifndef DSASA_ATOMS_NO_LAUNCH
+// Fast pass (64 planes, 64 vertex slots) over all atoms; the atoms it defers get the
+// 128 / 128 pass, whose grid reads the deferred count from device memory (no host sync).
 template <class R>
 cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     int blocks = (a.n + WARPS - 1) / WARPS;
-    if (grad && a.rec == nullptr) k_atoms<R, true><<<blocks, WARPS * 32, 0, s>>>(a);
-    else k_atoms<R, false><<<blocks, WARPS * 32, 0, s>>>(a);
+    AtomArgs fast = a;
+    fast.work_list = nullptr;
+    fast.work_count = nullptr;
+    AtomArgs big = a;
+    big.defer_list = nullptr;
+    big.defer_count = nullptr;
+    big.work_list = a.defer_list;
+    big.work_count = a.defer_count;
+    int big_blocks = blocks < 2048 ? blocks : 2048;
+    if (a.defer_count) cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
+    const bool g = grad && a.rec == nullptr;
+    if (g) k_atoms<R, true, 64, 64><<<blocks, WARPS * 32, 0, s>>>(fast);
+    else k_atoms<R, false, 64, 64><<<blocks, WARPS * 32, 0, s>>>(fast);
+    if (a.defer_list) {
+        if (g) k_atoms<R, true, 128, 128><<<big_blocks, WARPS * 32, 0, s>>>(big);
+        else k_atoms<R, false, 128, 128><<<big_blocks, WARPS * 32, 0, s>>>(big);
+    }
     return cudaGetLastError();
 }
-
 #endif
 
 }  // namespace dsasa

@@ -37,7 +37,8 @@ struct dsasa_ctx {
     int* cstart = nullptr;
     int* blocksums = nullptr;
     long long* offsets = nullptr;
-    int* status = nullptr;      // [0] status bits, [1] total cells
+    int* defer = nullptr;       // atoms the fast kernel pass defers to the large pass
+    int* status = nullptr;      // [0] status bits, [1] total cells, [2] deferred count
     unsigned long long* nrec = nullptr;
     // staging for the host-buffer entry point
     int64_t cap_host = 0;
@@ -76,6 +77,7 @@ template <class T> void dfree(T*& p) {
 void free_scratch(dsasa_ctx* c) {
     dfree(c->R); dfree(c->f4); dfree(c->molid); dfree(c->rank); dfree(c->cell); dfree(c->sidx); dfree(c->sf4);
     dfree(c->bbox); dfree(c->grids); dfree(c->counts); dfree(c->cstart); dfree(c->blocksums); dfree(c->offsets);
+    dfree(c->defer);
     c->cap_atoms = c->cap_mol = c->cap_cells = 0;
 }
 void free_host_staging(dsasa_ctx* c) {
@@ -107,7 +109,7 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
     if (e != cudaSuccess) { free_scratch(c); return cuda_fail(c, e, "cudaMalloc " #ptr); }
     ALLOC(R, na) ALLOC(f4, na) ALLOC(molid, na) ALLOC(rank, na) ALLOC(cell, na) ALLOC(sidx, na) ALLOC(sf4, na)
     ALLOC(bbox, 8 * nm) ALLOC(grids, nm) ALLOC(counts, nc + 1) ALLOC(cstart, nc + 1) ALLOC(blocksums, nbs)
-    ALLOC(offsets, nm + 1)
+    ALLOC(offsets, nm + 1) ALLOC(defer, na)
 #undef ALLOC
     c->cap_atoms = na;
     c->cap_mol = nm;
@@ -150,6 +152,8 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     a.rec = rec;
     a.max_rec = max_rec;
     a.nrec = c->nrec;
+    a.defer_list = c->defer;
+    a.defer_count = c->status + 2;
     e = c->cfg.precision == DSASA_FP64 ? launch_atoms_f64(a, grad != nullptr, c->stream)
                                        : launch_atoms_f32(a, grad != nullptr, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "atom kernel launch");

@@ -71,6 +71,12 @@ struct AtomArgs {
     int* rec;
     long long max_rec;
     unsigned long long* nrec;
+    // deferral: the fast pass appends sorted positions it cannot hold to defer_list; the
+    // large pass reads work_list[0 .. *work_count)
+    int* defer_list;
+    int* defer_count;
+    const int* work_list;
+    const int* work_count;
 };
 
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t s);

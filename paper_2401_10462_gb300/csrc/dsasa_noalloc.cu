@@ -37,7 +37,8 @@ constexpr size_t OFF_GRID = al(OFF_BBOX + sizeof(unsigned) * 8);
 constexpr size_t OFF_COUNTS = al(OFF_GRID + sizeof(MolGrid));
 constexpr size_t OFF_CSTART = al(OFF_COUNTS + sizeof(int) * (kMaxCells + 1));
 constexpr size_t OFF_BSUM = al(OFF_CSTART + sizeof(int) * (kMaxCells + 1));
-constexpr size_t OFF_STATUS = al(OFF_BSUM + sizeof(int) * 4096);
+constexpr size_t OFF_DEFER = al(OFF_BSUM + sizeof(int) * 4096);
+constexpr size_t OFF_STATUS = al(OFF_DEFER + sizeof(int) * kMaxAtoms);
 constexpr size_t kScratchBytes = al(OFF_STATUS + sizeof(int) * 4);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -111,6 +112,8 @@ extern "C" dsasa_status dsasa_compute_noalloc(const double* coords, const double
     a.grad = grad_out;
     a.n = (int)n;
     a.status = status;
+    a.defer_list = (int*)(base + OFF_DEFER);
+    a.defer_count = status + 2;
     if (launch_atoms_f32(a, grad_out != nullptr, s) != cudaSuccess) return DSASA_ERR_CUDA;
     int h = 0;
     if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return DSASA_ERR_CUDA;

@@ -77,18 +77,24 @@ typedef struct {
     int *cellof; /* per atom: its cell */
 } grid_t;
 
-static int grid_init(grid_t *g, double half, int cap) {
+/* grid over the box [lo, hi] (per axis) padded by one cell */
+static int grid_init_box(grid_t *g, const double *lo, const double *hi, int cap) {
     for (int k = 0; k < 3; ++k) {
-        g->lo[k] = -half - CELL;
-        g->dim[k] = (int)((2.0 * half + 2.0 * CELL) / CELL) + 1;
+        g->lo[k] = lo[k] - CELL;
+        g->dim[k] = (int)((hi[k] - lo[k] + 2.0 * CELL) / CELL) + 1;
     }
-    size_t nc = (size_t)g->dim[0] * g->dim[1] * g->dim[2];
+    size_t nc = (size_t)g->dim[0] * (size_t)g->dim[1] * (size_t)g->dim[2];
+    if (nc > ((size_t)1 << 31)) return -1;
     g->head = (int *)malloc(nc * sizeof(int));
     g->next = (int *)malloc((size_t)cap * sizeof(int));
     g->cellof = (int *)malloc((size_t)cap * sizeof(int));
     if (!g->head || !g->next || !g->cellof) return -1;
     for (size_t c = 0; c < nc; ++c) g->head[c] = -1;
     return 0;
+}
+static int grid_init(grid_t *g, double half, int cap) {
+    double lo[3] = {-half, -half, -half}, hi[3] = {half, half, half};
+    return grid_init_box(g, lo, hi, cap);
 }
 static void grid_free(grid_t *g) { free(g->head); free(g->next); free(g->cellof); }
 static int grid_cell(const grid_t *g, const double *p, int *ijk) {
@@ -97,22 +103,35 @@ static int grid_cell(const grid_t *g, const double *p, int *ijk) {
         if (c < 0 || c >= g->dim[k]) return -1;
         ijk[k] = c;
     }
-    return (ijk[2] * g->dim[1] + ijk[1]) * g->dim[0] + ijk[0];
+    return (int)(((long long)ijk[2] * g->dim[1] + ijk[1]) * g->dim[0] + ijk[0]);
 }
 static void grid_insert(grid_t *g, const double *p, int id) {
     int ijk[3];
     int c = grid_cell(g, p, ijk);
     g->cellof[id] = c;
+    if (c < 0) { g->next[id] = -1; return; }   /* callers only insert points inside the grid */
     g->next[id] = g->head[c];
     g->head[c] = id;
 }
 /* remove the most recently inserted atom id (it is the head of its cell) */
 static void grid_pop(grid_t *g, int id) {
     int c = g->cellof[id];
+    if (c < 0) return;
     if (g->head[c] == id) { g->head[c] = g->next[id]; return; }
     int a = g->head[c];
     while (a >= 0 && g->next[a] != id) a = g->next[a];
     if (a >= 0) g->next[a] = g->next[id];
+}
+/* remove atom id from its cell if it is linked there (no-op otherwise) */
+static void grid_pop_if(grid_t *g, int id) {
+    int c = g->cellof[id];
+    if (c < 0) return;
+    for (int a = g->head[c], prev = -1; a >= 0; prev = a, a = g->next[a])
+        if (a == id) {
+            if (prev < 0) g->head[c] = g->next[a]; else g->next[prev] = g->next[a];
+            g->cellof[id] = -1;
+            return;
+        }
 }
 /* 1 if p keeps the minimum distances to all placed atoms (ignoring the last bonded ones) */
 static int grid_clear(const grid_t *g, const double *xyz, const double *p, int self, int chain_lo) {
@@ -123,7 +142,7 @@ static int grid_clear(const grid_t *g, const double *xyz, const double *p, int s
             for (int dx = -1; dx <= 1; ++dx) {
                 int x = ijk[0] + dx, y = ijk[1] + dy, z = ijk[2] + dz;
                 if (x < 0 || y < 0 || z < 0 || x >= g->dim[0] || y >= g->dim[1] || z >= g->dim[2]) continue;
-                for (int a = g->head[(z * g->dim[1] + y) * g->dim[0] + x]; a >= 0; a = g->next[a]) {
+                for (int a = g->head[((long long)z * g->dim[1] + y) * g->dim[0] + x]; a >= 0; a = g->next[a]) {
                     double ex = p[0] - xyz[3 * a], ey = p[1] - xyz[3 * a + 1], ez = p[2] - xyz[3 * a + 2];
                     double d2 = ex * ex + ey * ey + ez * ez;
                     int sep = self - a; /* chain separation when a is in the same chain */
@@ -163,7 +182,7 @@ static int grow_chain(rng_t *r, grid_t *g, double *xyz, int start, int len, cons
             double u[3];
             rng_dir(r, u);
             if (bias) {
-                u[0] += 0.7 * bias[0]; u[1] += 0.7 * bias[1]; u[2] += 0.7 * bias[2];
+                u[0] += 0.3 * bias[0]; u[1] += 0.3 * bias[1]; u[2] += 0.3 * bias[2];
                 double s = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
                 if (s < 1e-6) continue;
                 u[0] /= s; u[1] /= s; u[2] /= s;
@@ -181,7 +200,7 @@ static int grow_chain(rng_t *r, grid_t *g, double *xyz, int start, int len, cons
         /* back off further the longer the walk stays stuck */
         int back = 3 + fails / 20;
         if (back > 60) back = 60;
-        while (back-- > 0 && i - 1 > start) { --i; grid_pop(g, i); }
+        while (back-- > 0 && i - 1 > start) { --i; grid_pop(g, i); g->cellof[i] = -1; }
     }
     return 0;
 }
@@ -275,9 +294,10 @@ double molgen_rna(int n, uint64_t seed, double *xyz, double *radii) {
     const double helix_r = 20.0, rise = 3.4, per_nt = 32;
     int n_nt = (n + 31) / 32;
     int per_strand = (n_nt + 1) / 2;
-    double half = helix_r + 4.0 + rise * per_strand;
+    double blo[3] = {-(helix_r + 4.0), -(helix_r + 4.0), -6.0};
+    double bhi[3] = {helix_r + 4.0, helix_r + 4.0, rise * per_strand + 6.0};
     grid_t g;
-    if (grid_init(&g, half, n) != 0) return -1.0;
+    if (grid_init_box(&g, blo, bhi, n) != 0) return -1.0;
     /* step angle 36 degrees: cos/sin by exact rotation recurrence would drift; use a table of
      * the ten angles computed once from rational constructions via sqrt only. */
     double c36 = (1.0 + sqrt(5.0)) / 4.0;            /* cos 36 */
@@ -288,30 +308,31 @@ double molgen_rna(int n, uint64_t seed, double *xyz, double *radii) {
         ca[k] = ca[k - 1] * c36 - sa[k - 1] * s36;
         sa[k] = sa[k - 1] * c36 + ca[k - 1] * s36;
     }
-    int placed = 0;
-    for (int nt = 0; nt < n_nt && placed < n; ++nt) {
+    /* backbone P atoms first (they are >= 12 A apart), then each nucleotide's chain grows
+       from its P atom avoiding everything placed so far */
+    for (int nt = 0, start = 0; nt < n_nt && start < n; ++nt, start += (int)per_nt) {
         int strand = nt & 1, k = nt >> 1;
         double sgn = strand ? -1.0 : 1.0; /* 180 degree phase shift */
-        double px = sgn * helix_r * ca[k % 10], py = sgn * helix_r * sa[k % 10];
-        double pz = rise * k;
-        int len = n - placed < (int)per_nt ? n - placed : (int)per_nt;
-        conf_t c = {CONF_SLAB, 0, 0, helix_r + 2.0, pz - 4.5, pz + 4.5};
-        double p[3] = {px, py, pz};
-        int start = placed;
-        /* the backbone point may clash with the other strand's previous nucleotide: nudge outward in z */
-        int ok = 0;
-        for (int t = 0; t < 200 && !ok; ++t) {
-            if (grid_clear(&g, xyz, p, start, start)) ok = 1;
-            else { p[0] = px + 1.0 * rng_sym(&r); p[1] = py + 1.0 * rng_sym(&r); p[2] = pz + 1.5 * rng_sym(&r); }
-        }
-        if (!ok) { grid_free(&g); return -1.0; }
+        double p[3] = {sgn * helix_r * ca[k % 10], sgn * helix_r * sa[k % 10], rise * k};
         xyz[3 * start] = p[0]; xyz[3 * start + 1] = p[1]; xyz[3 * start + 2] = p[2];
         grid_insert(&g, p, start);
         radii[start] = 1.9;
+    }
+    for (int nt = 0, start = 0; nt < n_nt && start < n; ++nt, start += (int)per_nt) {
+        int len = n - start < (int)per_nt ? n - start : (int)per_nt;
+        if (len <= 1) continue;
+        double px = xyz[3 * start], py = xyz[3 * start + 1], pz = xyz[3 * start + 2];
         double inward[3] = {-px / helix_r, -py / helix_r, 0.0};
-        if (len > 1 && grow_chain(&r, &g, xyz, start, len, &c, inward, 200) != 0) { grid_free(&g); return -1.0; }
+        int ok_nt = 0;
+        /* a crowded nucleotide is regrown; after a few failures its slab widens */
+        for (int attempt = 0; attempt < 24 && !ok_nt; ++attempt) {
+            double widen = attempt < 4 ? 0.0 : 0.5 * (attempt - 3);
+            conf_t c = {CONF_SLAB, 0, 0, helix_r + 2.0 + widen, pz - 4.5 - widen, pz + 4.5 + widen};
+            if (grow_chain(&r, &g, xyz, start, len, &c, inward, 200) == 0) ok_nt = 1;
+            else for (int id = start + len - 1; id > start; --id) grid_pop_if(&g, id);
+        }
+        if (!ok_nt) { grid_free(&g); return -1.0; }
         assign_radii(&r, radii, start + 1, len - 1, RNA_R, RNA_C, 4);
-        placed += len;
     }
     grid_free(&g);
     jitter(&r, xyz, n);

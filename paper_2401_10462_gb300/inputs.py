@@ -137,8 +137,32 @@ def serving_requests(count: int = 4096, seed: int = 0, lo: int = 300, hi: int = 
     return [(str(k), int(s), int(sd)) for k, s, sd in zip(kinds, sizes, seeds)]
 
 
-def make(kind: str, n: int, seed: int) -> Molecule:
-    return {"globule": globule, "rna": rna, "shell": shell}[kind](n, seed)
+def _cache_dir():
+    import tempfile
+    return os.environ.get("DSASA_INPUT_CACHE", os.path.join(tempfile.gettempdir(), "dsasa_inputs"))
+
+
+def make(kind: str, n: int, seed: int, cache: bool = True) -> Molecule:
+    """Generate (or load from the on-disk cache, for n >= 10,000) one molecule."""
+    gen = {"globule": globule, "rna": rna, "shell": shell}[kind]
+    if not cache or n < 10000:
+        return gen(n, seed)
+    path = os.path.join(_cache_dir(), f"{kind}_{n}_{seed}.npz")
+    if os.path.exists(path):
+        try:
+            d = np.load(path)
+            return Molecule(kind, d["coords"], d["radii"], seed, float(d["extent"]))
+        except Exception:
+            pass
+    m = gen(n, seed)
+    try:
+        os.makedirs(_cache_dir(), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}.npz"
+        np.savez(tmp, coords=m.coords, radii=m.radii, extent=m.extent)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return m
 
 
 def poisson_arrivals(count: int, rate_per_s: float, seed: int = 0) -> np.ndarray:
