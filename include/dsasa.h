@@ -114,6 +114,11 @@ dsasa_status dsasa_compute_host(dsasa_ctx* ctx, const double* coords_host, const
  * previous dsasa_status_sync (then clears it).  DSASA_OK if every atom was resolved. */
 dsasa_status dsasa_status_sync(dsasa_ctx* ctx);
 
+/* Diagnostics (no paper counterpart): synchronises the stream and writes to *deferred how
+ * many atoms of the most recent compute call had a cell larger than the fast pass holds
+ * (64 neighbour planes or 64 cell vertices) and were finished by the large-capacity pass. */
+dsasa_status dsasa_deferred_count(dsasa_ctx* ctx, int64_t* deferred);
+
 /* Diagnostic export of the dual complex C as seen by each atom's local cell.  For every atom
  * i and every simplex of C that contains i, one record of 5 int32 is written to `records`
  * (device, capacity `max_records`): {i, v0, v1, v2, v3} with the simplex's atom indices in

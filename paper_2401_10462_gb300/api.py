@@ -45,18 +45,20 @@ _lib.dsasa_compute_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_
                                      _vp, _vp, _vp]
 _lib.dsasa_compute_host.argtypes = [_vp, _dp, _dp, ctypes.c_double, _i64, _dp, _dp, _dp]
 _lib.dsasa_status_sync.argtypes = [_vp]
+_lib.dsasa_deferred_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_export_complex.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_last_error.argtypes = [_vp]
 _lib.dsasa_last_error.restype = ctypes.c_char_p
 _lib.dsasa_destroy.argtypes = [_vp]
 _lib.dsasa_version.restype = ctypes.c_char_p
 for _f in ("dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute", "dsasa_compute_vjp",
-           "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync", "dsasa_export_complex"):
+           "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync", "dsasa_export_complex",
+           "dsasa_deferred_count"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 EXPORTED = ("dsasa_default_config", "dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute",
             "dsasa_compute_vjp", "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync",
-            "dsasa_export_complex", "dsasa_last_error", "dsasa_destroy", "dsasa_version")
+            "dsasa_export_complex", "dsasa_last_error", "dsasa_destroy", "dsasa_version", "dsasa_deferred_count")
 
 
 class DSASAError(RuntimeError):
@@ -171,6 +173,12 @@ class Context:
     def status_sync(self):
         """Synchronise and raise if a device-side error was recorded since the last call."""
         self._raise(_lib.dsasa_status_sync(self._h))
+
+    def deferred_count(self) -> int:
+        """Atoms of the last call whose cell went to the large-capacity pass."""
+        d = ctypes.c_int64(0)
+        self._raise(_lib.dsasa_deferred_count(self._h, ctypes.byref(d)))
+        return int(d.value)
 
     def status_code(self) -> int:
         return _lib.dsasa_status_sync(self._h)

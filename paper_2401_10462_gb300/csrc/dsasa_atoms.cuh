@@ -33,7 +33,14 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int NG = 6;            // ghost planes (the initial cube)
 constexpr uint8_t NONE = 0xff;
-constexpr int WARPS = 4;         // warps per block
+constexpr int WARPS = 1;         // warps per block: a warp that finishes frees its slot at once
+constexpr int MINB = 32;         // resident blocks per SM the register budget is sized for
+
+// kernel phases: the whole computation in one kernel, or the cell construction (gather,
+// sort, clipping) and the classification + terms + gradient as two kernels that pass the
+// cell through a global record per atom (each kernel's code then fits the instruction cache)
+enum { PH_ALL = 0, PH_CELL = 1, PH_TERMS = 2 };
+enum { CELL_OK = 0, CELL_DONE = 1 };   // record flag: CELL_DONE = outputs already written
 
 // Per-warp cell storage.  NE plane entries (0..5 ghosts, then the candidates in sorted
 // order), NT cell-vertex slots (NT / 32 per lane).  Two capacities are compiled: 64 / 64
@@ -60,6 +67,18 @@ template <class R, int NE, int NT> struct Smem {
     uint8_t rsl[NT];      // removed slots in order
     uint8_t fs[NT];       // free slot stack
     int hw, nfree, bad;
+};
+
+// The cell of one atom between the two kernels (first NG + nc plane entries, first hw
+// vertex slots used).
+template <class R, int NE, int NT> struct CellRec {
+    R pq[NE][4];
+    R pB[NE];
+    int pg[NE];
+    uchar4 tv[NT];
+    uchar4 ta[NT];
+    uint8_t start[NE];
+    int nc, hw, flag, pad;
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -165,6 +184,15 @@ template <class SM, class R = typename SM::Real> __device__ __forceinline__ Plan
     P.b = {S->pq[e][3], S->pB[e]};
     return P;
 }
+// homogeneous cell vertex (Dv, D) of the planes of triangle v, with magnitudes for the filter
+template <class R> struct VtxFA { R v[4], a[4]; };
+template <class SM, class R = typename SM::Real> __device__ __noinline__ VtxFA<R> vertex_fa(const SM* S, uchar4 v) {
+    PlaneN<FA<R>> Pa = fplane(S, v.x), Pb = fplane(S, v.y), Pc = fplane(S, v.z);
+    V3<FA<R>> Dv;
+    FA<R> D;
+    vertex_hom(Pa, Pb, Pc, Dv, D);
+    return {{Dv.x.v, Dv.y.v, Dv.z.v, D.v}, {Dv.x.a, Dv.y.a, Dv.z.a, D.a}};
+}
 template <class R> struct Gam;
 template <> struct Gam<float> {
     static constexpr float g = G32, gclip = G32_CLIP, tiny = TINY32;
@@ -187,7 +215,7 @@ template <int KIND, class N> __device__ __forceinline__ N eval_k(const PlaneN<N>
 
 // sign of predicate KIND on shared-table planes e0..e3 (FP32/FP64 filter, then slow path)
 template <int KIND, class SM, class R = typename SM::Real>
-__device__ int psign(const SM* S, const Ctx& c, const FA<R>& wi, int e0, int e1, int e2 = 0, int e3 = 0) {
+__device__ __noinline__ int psign(const SM* S, const Ctx& c, const FA<R>& wi, int e0, int e1, int e2 = 0, int e3 = 0) {
     PlaneN<FA<R>> P[4] = {fplane(S, e0), fplane(S, e1), fplane(S, e2), fplane(S, e3)};
     int s = fa_sign(eval_k<KIND>(P, wi), Gam<R>::g, Gam<R>::tiny);
     if (s != 0) return s;
@@ -202,8 +230,8 @@ template <class SM, class R = typename SM::Real> __device__ __forceinline__ P3<R
 }
 
 // ------------------------------------------------------------------ the kernel
-template <class R, bool GRAD, int NE, int NT>
-__global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
+template <class R, bool GRAD, int NE, int NT, int PH>
+__global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
     constexpr int SPL = NT / 32;      // vertex slots per lane
     constexpr int KMAX = NE - NG;     // overlapping neighbours per atom
     const bool EXPORT = A.rec != nullptr;
@@ -234,9 +262,23 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
         c.status = A.status;
         const R Rr = (R)c.Ri;
         const FA<R> wi = {Rr * Rr, Rr * Rr};
+        CellRec<R, NE, NT>* rec = (CellRec<R, NE, NT>*)A.cells + s;
+        auto done = [&]() {   // the outputs of this atom are written: tell the terms kernel
+            if (PH == PH_CELL && lane == 0) rec->flag = CELL_DONE;
+        };
 
-        // ---------------- neighbour candidates: balls that may overlap B_i
         int nc = 0;
+        int nrounds = 1;     // vertex-slot rounds in use: slots < 32 * nrounds (warp-uniform)
+        // per-lane vertex caches (homogeneous z = Dv / D with magnitudes for the filter)
+        R V[SPL][4], Va[SPL][4];
+        unsigned alive = 0;
+        auto compute_vertex = [&](int r, int t) {
+            VtxFA<R> q = vertex_fa(S, S->tv[t]);
+            for (int k = 0; k < 4; ++k) { V[r][k] = q.v[k]; Va[r][k] = q.a[k]; }
+        };
+
+        if constexpr (PH != PH_TERMS) {
+        // ---------------- neighbour candidates: balls that may overlap B_i
         {
             int cx = min(max((int)floorf((fi.x - G.lo[0]) * G.inv_cell), 0), G.dims[0] - 1);
             int cy = min(max((int)floorf((fi.y - G.lo[1]) * G.inv_cell), 0), G.dims[1] - 1);
@@ -271,6 +313,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
         }
         if (nc > KMAX && can_defer) {
             if (lane == 0) A.defer_list[atomicAdd(A.defer_count, 1)] = s;
+            done();
             __syncwarp();
             continue;
         }
@@ -280,6 +323,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
                 A.areas[i] = __longlong_as_double(0x7ff8000000000000ll);
                 if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
             }
+            done();
             __syncwarp();
             continue;
         }
@@ -414,18 +458,6 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
         if (lane < NG) S->start[lane] = (lane & 1) ? 7 : 0;   // +x,+y,+z at corner 0; -x,-y,-z at 7
         __syncwarp();
 
-        // per-lane vertex caches (homogeneous z = Dv / D with magnitudes for the filter)
-        R V[SPL][4], Va[SPL][4];
-        unsigned alive = 0;
-        auto compute_vertex = [&](int r, int t) {
-            uchar4 v = S->tv[t];
-            PlaneN<FA<R>> Pa = fplane(S, v.x), Pb = fplane(S, v.y), Pc = fplane(S, v.z);
-            V3<FA<R>> Dv;
-            FA<R> D;
-            vertex_hom(Pa, Pb, Pc, Dv, D);
-            V[r][0] = Dv.x.v; V[r][1] = Dv.y.v; V[r][2] = Dv.z.v; V[r][3] = D.v;
-            Va[r][0] = Dv.x.a; Va[r][1] = Dv.y.a; Va[r][2] = Dv.z.a; Va[r][3] = D.a;
-        };
 #pragma unroll
         for (int r = 0; r < SPL; ++r) {
             int t = r * 32 + lane;
@@ -435,7 +467,6 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
         // ---------------- clipping by the sorted neighbour planes
         bool empty = false;
         int nalive = 8;      // live cell vertices (warp-uniform)
-        int nrounds = 1;     // vertex-slot rounds in use: slots < 32 * nrounds (warp-uniform)
         for (int kk = 0; kk < nc && !empty; ++kk) {
             const int m = S->ord[kk] & (NE - 1);
             const PlaneN<FA<R>> M = fplane(S, m);
@@ -572,6 +603,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
         const bool bad = S->bad != 0;
         if (bad && S->bad == 2 && can_defer) {
             if (lane == 0) A.defer_list[atomicAdd(A.defer_count, 1)] = s;
+            done();
             __syncwarp();
             continue;
         }
@@ -581,6 +613,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
                 A.areas[i] = __longlong_as_double(0x7ff8000000000000ll);
                 if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
             }
+            done();
             __syncwarp();
             continue;
         }
@@ -590,8 +623,56 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
                 A.areas[i] = 0.0;
                 if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = 0.0; }
             }
+            done();
             __syncwarp();
             continue;
+        }
+        if constexpr (PH == PH_CELL) {
+            // hand the cell to the terms kernel
+            const int np = NG + nc, hw = S->hw;
+            for (int e = lane; e < np; e += 32) {
+                for (int k = 0; k < 4; ++k) rec->pq[e][k] = S->pq[e][k];
+                rec->pB[e] = S->pB[e];
+                rec->pg[e] = S->pg[e];
+                rec->start[e] = S->start[e];
+            }
+            for (int t = lane; t < hw; t += 32) {
+                rec->tv[t] = S->tv[t];
+                rec->ta[t] = S->ta[t];
+            }
+            if (lane == 0) {
+                rec->nc = nc;
+                rec->hw = hw;
+                rec->flag = CELL_OK;
+            }
+            __syncwarp();
+            continue;
+        }
+        } else {
+            // ---------------- the cell built by the cell kernel
+            if (rec->flag != CELL_OK) continue;
+            nc = rec->nc;
+            const int np = NG + nc, hw = rec->hw;
+            nrounds = (hw + 31) >> 5;
+            for (int e = lane; e < np; e += 32) {
+                for (int k = 0; k < 4; ++k) S->pq[e][k] = rec->pq[e][k];
+                S->pB[e] = rec->pB[e];
+                S->pg[e] = rec->pg[e];
+                S->start[e] = rec->start[e];
+            }
+            for (int t = lane; t < 32 * nrounds; t += 32) {
+                S->tv[t] = t < hw ? rec->tv[t] : make_uchar4(NONE, NONE, NONE, 0);
+                S->ta[t] = t < hw ? rec->ta[t] : make_uchar4(NONE, NONE, NONE, 0);
+            }
+            if (lane == 0) { S->hw = hw; S->bad = 0; }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < SPL; ++r) {
+                if (r >= nrounds) break;
+                int t = r * 32 + lane;
+                if (S->tv[t].x != NONE) { compute_vertex(r, t); alive |= 1u << r; }
+            }
+            __syncwarp();
         }
 
         // ---------------- Step 2a: tetrahedra of C (cell vertices inside B_i)
@@ -683,12 +764,10 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
                     if (S->kf[t] == 1) {
                         ++nk;
                         P3<R> pb = ppos(S, b), pc = ppos(S, cc);
-                        phi_sum += (double)dihedral(O, pa, pb, pc);
+                        phi_sum += (double)dihedral_ol(O, pa, pb, pc);
                         if (GRAD) {
                             // (i, a, b, c) is positively oriented: (a, b, c) is counter-clockwise
-                            P3<R> gu, gv, gc, gd;
-                            dihedral_grad_s(O, pa, pb, pc, (R)1, gu, gv, gc, gd);
-                            gsum = gsum + gu;
+                            gsum = gsum + dihedral_grad_u_ol(O, pa, pb, pc, (R)1);
                         }
                     }
                     if ((S->tf[t] >> k) & 1) triK = true;
@@ -768,7 +847,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
             for (int r = 0; r < SPL; ++r) {
                 if (!(kmask >> r & 1)) continue;
                 uchar4 v = S->tv[r * 32 + lane];
-                om += (double)solid_angle_half(ppos(S, v.x), ppos(S, v.y), ppos(S, v.z));
+                om += (double)solid_angle_half_ol(ppos(S, v.x), ppos(S, v.y), ppos(S, v.z));
             }
             om = warp_sum_d(om);
             if (lane == 0) area_acc += (1.0 - om / TWO_PI) * 2.0 * TWO_PI * c.Ri * c.Ri;
@@ -807,22 +886,21 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
                 P3<R> pa = ppos(S, a), pb = ppos(S, b);
                 int ga = S->pg[a], gb = S->pg[b];
                 double Ra = A.R[ga], Rb = A.R[gb];
-                area_acc += cf * tri_term_mixed(pa, pb, c.Ri, Ra, Rb);
+                area_acc += cf * tri_term_mixed_ol(pa, pb, c.Ri, Ra, Rb);
                 if (GRAD) {
                     const P3<R> O = {zero, zero, zero};
                     double wa = A.w ? A.w[ga] : 1.0, wb = A.w ? A.w[gb] : 1.0;
                     R Raf = (R)Ra, Rbf = (R)Rb;
-                    P3<R> g2, g3;
                     // owner i: d/dp_i = -(g2 + g3)
-                    lens_grad(pa, pb, Rr, Raf, Rbf, g2, g3);
-                    double sx = -wi_w * (double)(g2.x + g3.x), sy = -wi_w * (double)(g2.y + g3.y),
-                           sz = -wi_w * (double)(g2.z + g3.z);
+                    P3x2<R> lg = lens_grad_ol(pa, pb, Rr, Raf, Rbf);
+                    double sx = -wi_w * (double)(lg.a.x + lg.b.x), sy = -wi_w * (double)(lg.a.y + lg.b.y),
+                           sz = -wi_w * (double)(lg.a.z + lg.b.z);
                     // owner a: p_i is the second centre
-                    lens_grad(O - pa, pb - pa, Raf, Rr, Rbf, g2, g3);
-                    sx += wa * (double)g2.x; sy += wa * (double)g2.y; sz += wa * (double)g2.z;
+                    lg = lens_grad_ol(O - pa, pb - pa, Raf, Rr, Rbf);
+                    sx += wa * (double)lg.a.x; sy += wa * (double)lg.a.y; sz += wa * (double)lg.a.z;
                     // owner b
-                    lens_grad(O - pb, pa - pb, Rbf, Rr, Raf, g2, g3);
-                    sx += wb * (double)g2.x; sy += wb * (double)g2.y; sz += wb * (double)g2.z;
+                    lg = lens_grad_ol(O - pb, pa - pb, Rbf, Rr, Raf);
+                    sx += wb * (double)lg.a.x; sy += wb * (double)lg.a.y; sz += wb * (double)lg.a.z;
                     sx *= cf; sy *= cf; sz *= cf;
                     if (nk == 1) {
                         // the single tetrahedron of C on this triangle: (i, a, b, x); its
@@ -834,8 +912,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
                         double dab = (double)norm3(pb - pa);
                         double tab = (dab * dab + Ra * Ra - Rb * Rb) / (2.0 * dab), tba = dab - tab;
                         double kap = -(wa * Ra * tab + wb * Rb * tba);
-                        P3<R> gu, gv, gc, gd;
-                        dihedral_grad_s(pa, pb, O, ppos(S, x), on_t ? (R)1 : (R)-1, gu, gv, gc, gd);
+                        P3<R> gc = dihedral_grad_c_ol(pa, pb, O, ppos(S, x), on_t ? (R)1 : (R)-1);
                         sx += kap * (double)gc.x; sy += kap * (double)gc.y; sz += kap * (double)gc.z;
                     }
                     gx += sx;
@@ -902,8 +979,9 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_atoms(AtomArgs A) {
 }  // namespace
 
 #ifndef DSASA_ATOMS_NO_LAUNCH
-// Fast pass (64 planes, 64 vertex slots) over all atoms; the atoms it defers get the
-// 128 / 128 pass, whose grid reads the deferred count from device memory (no host sync).
+// Fast pass (64 planes, 64 vertex slots) over all atoms: with a cell store, the cell kernel
+// then the terms kernel, else the fused kernel.  The atoms it defers get the fused 128 / 128
+// pass, whose grid reads the deferred count from device memory (no host sync).
 template <class R>
 cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
@@ -916,14 +994,21 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     big.defer_count = nullptr;
     big.work_list = a.defer_list;
     big.work_count = a.defer_count;
-    int big_blocks = blocks < 2048 ? blocks : 2048;
+    big.cells = nullptr;
+    int big_blocks = blocks < 4096 ? blocks : 4096;
     if (a.defer_count) cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
     const bool g = grad && a.rec == nullptr;
-    if (g) k_atoms<R, true, 64, 64><<<blocks, WARPS * 32, 0, s>>>(fast);
-    else k_atoms<R, false, 64, 64><<<blocks, WARPS * 32, 0, s>>>(fast);
+    if (a.cells) {
+        k_atoms<R, false, 64, 64, PH_CELL><<<blocks, WARPS * 32, 0, s>>>(fast);
+        if (g) k_atoms<R, true, 64, 64, PH_TERMS><<<blocks, WARPS * 32, 0, s>>>(fast);
+        else k_atoms<R, false, 64, 64, PH_TERMS><<<blocks, WARPS * 32, 0, s>>>(fast);
+    } else {
+        if (g) k_atoms<R, true, 64, 64, PH_ALL><<<blocks, WARPS * 32, 0, s>>>(fast);
+        else k_atoms<R, false, 64, 64, PH_ALL><<<blocks, WARPS * 32, 0, s>>>(fast);
+    }
     if (a.defer_list) {
-        if (g) k_atoms<R, true, 128, 128><<<big_blocks, WARPS * 32, 0, s>>>(big);
-        else k_atoms<R, false, 128, 128><<<big_blocks, WARPS * 32, 0, s>>>(big);
+        if (g) k_atoms<R, true, 128, 128, PH_ALL><<<big_blocks, WARPS * 32, 0, s>>>(big);
+        else k_atoms<R, false, 128, 128, PH_ALL><<<big_blocks, WARPS * 32, 0, s>>>(big);
     }
     return cudaGetLastError();
 }

@@ -4,4 +4,9 @@
 
 namespace dsasa {
 cudaError_t launch_atoms_f32(const AtomArgs& a, bool grad, cudaStream_t s) { return launch_atoms_t<float>(a, grad, s); }
+// bytes of one atom's cell record between the two kernels (the larger of the two precisions)
+size_t cell_record_bytes() {
+    return sizeof(CellRec<double, 64, 64>) > sizeof(CellRec<float, 64, 64>) ? sizeof(CellRec<double, 64, 64>)
+                                                                            : sizeof(CellRec<float, 64, 64>);
+}
 }  // namespace dsasa

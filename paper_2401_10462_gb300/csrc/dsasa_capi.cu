@@ -38,6 +38,7 @@ struct dsasa_ctx {
     int* blocksums = nullptr;
     long long* offsets = nullptr;
     int* defer = nullptr;       // atoms the fast kernel pass defers to the large pass
+    unsigned char* cells = nullptr;   // per-atom cell records between the cell and terms kernels
     int* status = nullptr;      // [0] status bits, [1] total cells, [2] deferred count
     unsigned long long* nrec = nullptr;
     // staging for the host-buffer entry point
@@ -77,7 +78,7 @@ template <class T> void dfree(T*& p) {
 void free_scratch(dsasa_ctx* c) {
     dfree(c->R); dfree(c->f4); dfree(c->molid); dfree(c->rank); dfree(c->cell); dfree(c->sidx); dfree(c->sf4);
     dfree(c->bbox); dfree(c->grids); dfree(c->counts); dfree(c->cstart); dfree(c->blocksums); dfree(c->offsets);
-    dfree(c->defer);
+    dfree(c->defer); dfree(c->cells);
     c->cap_atoms = c->cap_mol = c->cap_cells = 0;
 }
 void free_host_staging(dsasa_ctx* c) {
@@ -109,7 +110,7 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
     if (e != cudaSuccess) { free_scratch(c); return cuda_fail(c, e, "cudaMalloc " #ptr); }
     ALLOC(R, na) ALLOC(f4, na) ALLOC(molid, na) ALLOC(rank, na) ALLOC(cell, na) ALLOC(sidx, na) ALLOC(sf4, na)
     ALLOC(bbox, 8 * nm) ALLOC(grids, nm) ALLOC(counts, nc + 1) ALLOC(cstart, nc + 1) ALLOC(blocksums, nbs)
-    ALLOC(offsets, nm + 1) ALLOC(defer, na)
+    ALLOC(offsets, nm + 1) ALLOC(defer, na) ALLOC(cells, na * (int64_t)cell_record_bytes())
 #undef ALLOC
     c->cap_atoms = na;
     c->cap_mol = nm;
@@ -154,6 +155,7 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     a.nrec = c->nrec;
     a.defer_list = c->defer;
     a.defer_count = c->status + 2;
+    a.cells = c->cells;
     e = c->cfg.precision == DSASA_FP64 ? launch_atoms_f64(a, grad != nullptr, c->stream)
                                        : launch_atoms_f32(a, grad != nullptr, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "atom kernel launch");
@@ -314,6 +316,17 @@ dsasa_status dsasa_status_sync(dsasa_ctx* c) {
     if (s & (ST_UNRESOLVED | ST_BADCELL))
         return fail(c, DSASA_ERR_UNRESOLVED, "an exact predicate or a cell could not be resolved (status 0x%x)", s);
     return fail(c, DSASA_ERR_DEGENERATE, "an exactly degenerate configuration was met (status 0x%x)", s);
+}
+
+dsasa_status dsasa_deferred_count(dsasa_ctx* c, int64_t* deferred) {
+    if (!c || !deferred) return DSASA_ERR_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    int h[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, c->status, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "deferred count read");
+    *deferred = h[2];
+    return DSASA_OK;
 }
 
 dsasa_status dsasa_export_complex(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,

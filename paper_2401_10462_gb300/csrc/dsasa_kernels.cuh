@@ -77,11 +77,15 @@ struct AtomArgs {
     int* defer_count;
     const int* work_list;
     const int* work_count;
+    // per-atom cell records (by sorted position) between the cell kernel and the terms
+    // kernel; NULL = one fused kernel
+    void* cells;
 };
 
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t s);
 cudaError_t launch_atoms_f32(const AtomArgs& a, bool grad, cudaStream_t s);
 cudaError_t launch_atoms_f64(const AtomArgs& a, bool grad, cudaStream_t s);
 size_t scan_scratch_ints(int max_cells);
+size_t cell_record_bytes();
 
 }  // namespace dsasa

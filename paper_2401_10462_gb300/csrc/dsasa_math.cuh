@@ -26,9 +26,11 @@
 #if defined(__CUDACC__)
 #define DS_HD __host__ __device__ __forceinline__
 #define DS_HDNI __host__ __device__ __noinline__ static
+#define DS_HDC __host__ __device__ __noinline__
 #else
 #define DS_HD inline
 #define DS_HDNI static
+#define DS_HDC inline
 #endif
 
 namespace dsasa {
@@ -491,6 +493,34 @@ template <class T> DS_HD void lens_grad(P3<T> q2, P3<T> q3, T R1, T R2, T R3, P3
     P3<T> w2 = (n3 - n2 * g) * ((T)1 / sg), w3 = (n2 - n3 * g) * ((T)1 / sg);
     g2 = (n2 * (-be2 * (d2 - t12)) + w2 * st) * ((T)2 * R1 / d2);
     g3 = (n3 * (-be3 * (d3 - t13)) + w3 * st) * ((T)2 * R1 / d3);
+}
+
+// ------------------------------------------------------------------ out-of-line forms
+// The kernels call the heavy terms through these (one copy of each body instead of one per
+// call site), which keeps the kernels small enough for the instruction cache.  Results are
+// returned by value so that no caller variable has to live in local memory.
+template <class T> struct P3x2 { P3<T> a, b; };
+template <class T> DS_HDC T dihedral_ol(P3<T> u, P3<T> v, P3<T> c, P3<T> d) { return dihedral(u, v, c, d); }
+// d theta / d u of dihedral_grad_s
+template <class T> DS_HDC P3<T> dihedral_grad_u_ol(P3<T> u, P3<T> v, P3<T> c, P3<T> d, T sg) {
+    P3<T> gu, gv, gc, gd;
+    dihedral_grad_s(u, v, c, d, sg, gu, gv, gc, gd);
+    return gu;
+}
+// d theta / d c of dihedral_grad_s
+template <class T> DS_HDC P3<T> dihedral_grad_c_ol(P3<T> u, P3<T> v, P3<T> c, P3<T> d, T sg) {
+    P3<T> gu, gv, gc, gd;
+    dihedral_grad_s(u, v, c, d, sg, gu, gv, gc, gd);
+    return gc;
+}
+template <class T> DS_HDC T solid_angle_half_ol(P3<T> a, P3<T> b, P3<T> c) { return solid_angle_half(a, b, c); }
+template <class T> DS_HDC double tri_term_mixed_ol(P3<T> p2, P3<T> p3, double R1, double R2, double R3) {
+    return tri_term_mixed(p2, p3, R1, R2, R3);
+}
+template <class T> DS_HDC P3x2<T> lens_grad_ol(P3<T> q2, P3<T> q3, T R1, T R2, T R3) {
+    P3x2<T> r;
+    lens_grad(q2, q3, R1, R2, R3, r.a, r.b);
+    return r;
 }
 
 }  // namespace dsasa

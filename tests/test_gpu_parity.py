@@ -180,10 +180,11 @@ def test_batch_equals_separate(api, torch_cuda, gen):
         assert np.array_equal(g.cpu().numpy()[off[k]:off[k + 1]], g1)
 
 
-def test_deterministic(api, torch_cuda, gen):
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_deterministic(api, torch_cuda, gen, precision):
     m = gen.globule(2000, 4)
-    r1 = gpu_sasa(api, torch_cuda, m.coords, m.radii)
-    r2 = gpu_sasa(api, torch_cuda, m.coords, m.radii)
+    r1 = gpu_sasa(api, torch_cuda, m.coords, m.radii, precision)
+    r2 = gpu_sasa(api, torch_cuda, m.coords, m.radii, precision)
     assert np.array_equal(r1[0], r2[0]) and np.array_equal(r1[1], r2[1])
 
 
@@ -202,10 +203,17 @@ def test_large_cells_take_the_deferred_pass(api, torch_cuda, orc, precision, m, 
     shell = shell[z > zcut]
     xyz = np.concatenate([np.zeros((1, 3)) + 1e-6, shell])
     r = np.concatenate([[3.6], np.full(len(shell), 1.2)])
-    a, g = gpu_sasa(api, torch_cuda, xyz, r, precision)
+    torch = torch_cuda
+    ctx = api.Context(precision=precision)
+    a = torch.empty(len(r), dtype=torch.float64, device="cuda")
+    g = torch.empty((len(r), 3), dtype=torch.float64, device="cuda")
+    ctx.compute(_dev(torch, xyz), _dev(torch, r), a, g)
+    assert ctx.deferred_count() >= 1   # the large ball went through the large-capacity pass
+    ctx.status_sync()
+    ctx.close()
     ra, _, rg = orc.sasa(xyz, r)
-    check_areas(a, ra)
-    check_grad(g, rg)
+    check_areas(a.cpu().numpy(), ra)
+    check_grad(g.cpu().numpy(), rg)
 
 
 def test_capsid_million_sampled_parity(api, torch_cuda, orc, gen):
