@@ -731,17 +731,20 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
         __syncwarp();
 
         // ---------------- Step 2c / 3: faces (edges of C), area terms, gradient gathers
-        // Vectors and angles are evaluated in R (float in the mixed mode); every scalar
-        // combination (normalisation by 2 pi, caps, coefficients, sums) is done in FP64.
+        // Vectors, angles and the gradient are evaluated in R (float in the mixed mode).  The
+        // area terms are combined in FP64 in a form where pi multiplies only quantities of the
+        // radii and distances (pi, R_i and R_i^2 rounded to float would bias every term the
+        // same way, and the terms cancel about 30-fold in A_i); no FP64 division is used.
         const R zero = (R)0;
         const double TWO_PI = 6.283185307179586476925;
         double area_acc = 0.0;
-        double gx = 0.0, gy = 0.0, gz = 0.0;
+        R gx = zero, gy = zero, gz = zero;
         const double wi_w = A.w ? A.w[i] : 1.0;
+        const R wif = (R)wi_w;
         int myEK = 0;
         for (int a = NG + lane; a < NG + nc; a += 32) {
             uint8_t flag = 0;
-            double phi_sum = 0.0;
+            R phi_sum = zero;
             int st = S->start[a];
             bool active = false;
             if (st != NONE) {
@@ -764,7 +767,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
                     if (S->kf[t] == 1) {
                         ++nk;
                         P3<R> pb = ppos(S, b), pc = ppos(S, cc);
-                        phi_sum += (double)dihedral_ol(O, pa, pb, pc);
+                        phi_sum += dihedral_ol(O, pa, pb, pc);
                         if (GRAD) {
                             // (i, a, b, c) is positively oriented: (a, b, c) is counter-clockwise
                             gsum = gsum + dihedral_grad_u_ol(O, pa, pb, pc, (R)1);
@@ -795,21 +798,27 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
                     flag = 1 | (closed ? 2 : 0);
                     myEK = 1;
                     if (!closed) {
-                        // edge term of A_i (Eqs. phiedge, edge): - Phi_ia S_ia^(i)
-                        double phi = 1.0 - phi_sum / TWO_PI;
+                        // edge term of A_i (Eqs. phiedge, edge): - Phi_ia S_ia^(i) with
+                        // S_ia^(i) = 2 pi R_i h_i and Phi_ia = 1 - sum(theta) / 2 pi, i.e.
+                        // R_i h_i (sum(theta) - 2 pi); h_i = (R_i + R_a - d)(R_a - R_i + d) / 2d
                         int ga = S->pg[a];
-                        double d = (double)norm3(pa), Ra = A.R[ga];
-                        area_acc -= phi * cap64(d, c.Ri, Ra);
+                        const double Ra = A.R[ga];
+                        const R dr = norm3(pa), inv2d = (R)0.5 / dr;
+                        const double d = (double)dr;
+                        const double hi = ((c.Ri + Ra) - d) * ((Ra - c.Ri) + d) * (double)inv2d;
+                        area_acc += c.Ri * hi * ((double)phi_sum - TWO_PI);
                         if (GRAD) {
-                            double wa = A.w ? A.w[ga] : 1.0;
-                            double ti = (d * d + c.Ri * c.Ri - Ra * Ra) / (2.0 * d), ta = d - ti;
+                            const R waf = (R)(A.w ? A.w[ga] : 1.0), Raf = (R)Ra;
+                            const R dR2 = (R)((c.Ri - Ra) * (c.Ri + Ra));
+                            const R ti = (dr * dr + dR2) * inv2d, ta = (dr * dr - dR2) * inv2d;
+                            const R phi = (R)1 - phi_sum * (R)(1.0 / TWO_PI);
                             // vertex + edge parts of the dihedral derivatives around ia (Eq. inexclu)
-                            double kap = -(wi_w * c.Ri * ti + wa * Ra * ta);
+                            const R kap = -(wif * Rr * ti + waf * Raf * ta);
                             // cap derivatives (Eq. edge): -Phi (2 pi / d)(w_i R_i t_a + w_a R_a t_i) u
-                            double cf = -phi * TWO_PI / (d * d) * (wi_w * c.Ri * ta + wa * Ra * ti);
-                            gx += kap * (double)gsum.x + cf * (double)pa.x;
-                            gy += kap * (double)gsum.y + cf * (double)pa.y;
-                            gz += kap * (double)gsum.z + cf * (double)pa.z;
+                            const R cf = -phi * (R)TWO_PI / (dr * dr) * (wif * Rr * ta + waf * Raf * ti);
+                            gx += kap * gsum.x + cf * pa.x;
+                            gy += kap * gsum.y + cf * pa.y;
+                            gz += kap * gsum.z + cf * pa.z;
                         }
                     }
                 }
@@ -841,16 +850,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
         }
 
         // vertex term Omega_i 4 pi R_i^2 (Eq. vertex), Omega_i = 1 - sum of solid angles / 4 pi
+        // (with the half solid angles h_T of its tetrahedra: Omega_i 4 pi R_i^2 = 4 pi R_i^2 - 2 R_i^2 sum h_T)
         if (iK && !icl) {
-            double om = 0.0;
+            R om = zero;
 #pragma unroll
             for (int r = 0; r < SPL; ++r) {
                 if (!(kmask >> r & 1)) continue;
                 uchar4 v = S->tv[r * 32 + lane];
-                om += (double)solid_angle_half_ol(ppos(S, v.x), ppos(S, v.y), ppos(S, v.z));
+                om += solid_angle_half_ol(ppos(S, v.x), ppos(S, v.y), ppos(S, v.z));
             }
-            om = warp_sum_d(om);
-            if (lane == 0) area_acc += (1.0 - om / TWO_PI) * 2.0 * TWO_PI * c.Ri * c.Ri;
+            double omd = warp_sum_d((double)om);
+            if (lane == 0) area_acc += c.Ri * c.Ri * (2.0 * TWO_PI - 2.0 * omd);
         }
 
         // triangle terms: c_iab S_iab^(i) (Eq. trianglev) and the gradient of the triangle
@@ -889,19 +899,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
                 area_acc += cf * tri_term_mixed_ol(pa, pb, c.Ri, Ra, Rb);
                 if (GRAD) {
                     const P3<R> O = {zero, zero, zero};
-                    double wa = A.w ? A.w[ga] : 1.0, wb = A.w ? A.w[gb] : 1.0;
-                    R Raf = (R)Ra, Rbf = (R)Rb;
+                    const R waf = (R)(A.w ? A.w[ga] : 1.0), wbf = (R)(A.w ? A.w[gb] : 1.0);
+                    const R Raf = (R)Ra, Rbf = (R)Rb, cff = (R)cf;
                     // owner i: d/dp_i = -(g2 + g3)
                     P3x2<R> lg = lens_grad_ol(pa, pb, Rr, Raf, Rbf);
-                    double sx = -wi_w * (double)(lg.a.x + lg.b.x), sy = -wi_w * (double)(lg.a.y + lg.b.y),
-                           sz = -wi_w * (double)(lg.a.z + lg.b.z);
+                    R sx = -wif * (lg.a.x + lg.b.x), sy = -wif * (lg.a.y + lg.b.y), sz = -wif * (lg.a.z + lg.b.z);
                     // owner a: p_i is the second centre
                     lg = lens_grad_ol(O - pa, pb - pa, Raf, Rr, Rbf);
-                    sx += wa * (double)lg.a.x; sy += wa * (double)lg.a.y; sz += wa * (double)lg.a.z;
+                    sx += waf * lg.a.x; sy += waf * lg.a.y; sz += waf * lg.a.z;
                     // owner b
                     lg = lens_grad_ol(O - pb, pa - pb, Rbf, Rr, Raf);
-                    sx += wb * (double)lg.a.x; sy += wb * (double)lg.a.y; sz += wb * (double)lg.a.z;
-                    sx *= cf; sy *= cf; sz *= cf;
+                    sx += wbf * lg.a.x; sy += wbf * lg.a.y; sz += wbf * lg.a.z;
+                    sx *= cff; sy *= cff; sz *= cff;
                     if (nk == 1) {
                         // the single tetrahedron of C on this triangle: (i, a, b, x); its
                         // orientation is + when it is the cell vertex t, - when it is t2
@@ -909,11 +918,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
                         uint8_t xo = (w.x != a && w.x != b) ? w.x : ((w.y != a && w.y != b) ? w.y : w.z);
                         bool on_t = S->kf[t] == 1;
                         uint8_t x = on_t ? cc : xo;
-                        double dab = (double)norm3(pb - pa);
-                        double tab = (dab * dab + Ra * Ra - Rb * Rb) / (2.0 * dab), tba = dab - tab;
-                        double kap = -(wa * Ra * tab + wb * Rb * tba);
+                        const R dab = norm3(pb - pa), inv2 = (R)0.5 / dab;
+                        const R dR2 = (R)((Ra - Rb) * (Ra + Rb));
+                        const R tab = (dab * dab + dR2) * inv2, tba = (dab * dab - dR2) * inv2;
+                        const R kap = -(waf * Raf * tab + wbf * Rbf * tba);
                         P3<R> gc = dihedral_grad_c_ol(pa, pb, O, ppos(S, x), on_t ? (R)1 : (R)-1);
-                        sx += kap * (double)gc.x; sy += kap * (double)gc.y; sz += kap * (double)gc.z;
+                        sx += kap * gc.x; sy += kap * gc.y; sz += kap * gc.z;
                     }
                     gx += sx;
                     gy += sy;
@@ -923,10 +933,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
         }
 
         area_acc = warp_sum_d(area_acc);
+        double gxd = 0.0, gyd = 0.0, gzd = 0.0;
         if (GRAD) {
-            gx = warp_sum_d(gx);
-            gy = warp_sum_d(gy);
-            gz = warp_sum_d(gz);
+            gxd = warp_sum_d((double)gx);
+            gyd = warp_sum_d((double)gy);
+            gzd = warp_sum_d((double)gz);
         }
         __syncwarp();
         if (lane == 0) {
@@ -936,9 +947,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
             }
             A.areas[i] = iK ? area_acc : 0.0;
             if (GRAD && A.grad) {
-                A.grad[3 * i] = iK ? gx : 0.0;
-                A.grad[3 * i + 1] = iK ? gy : 0.0;
-                A.grad[3 * i + 2] = iK ? gz : 0.0;
+                A.grad[3 * i] = iK ? gxd : 0.0;
+                A.grad[3 * i + 1] = iK ? gyd : 0.0;
+                A.grad[3 * i + 2] = iK ? gzd : 0.0;
             }
         }
 

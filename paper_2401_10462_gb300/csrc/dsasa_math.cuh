@@ -460,9 +460,12 @@ template <class T> DS_HD double tri_term_mixed(P3<T> p2, P3<T> p3, double R1, do
     const P3<T> O = {(T)0, (T)0, (T)0};
     P3<T> x;
     triple_point(O, p2, p3, (T)R1, (T)R2, (T)R3, x);
-    double d12 = (double)norm3(p2), d13 = (double)norm3(p3);
-    double t12 = (d12 * d12 + R1 * R1 - R2 * R2) / (2.0 * d12);
-    double t13 = (d13 * d13 + R1 * R1 - R3 * R3) / (2.0 * d13);
+    // t1k = (d1k^2 + R1^2 - Rk^2) / 2 d1k with the radii part in FP64 and the reciprocal of
+    // the distance in T (its rounding differs from triangle to triangle: no systematic bias)
+    const T e12 = norm3(p2), e13 = norm3(p3);
+    const double d12 = (double)e12, d13 = (double)e13;
+    double t12 = (d12 * d12 + (R1 - R2) * (R1 + R2)) * (double)((T)0.5 / e12);
+    double t13 = (d13 * d13 + (R1 - R3) * (R1 + R3)) * (double)((T)0.5 / e13);
     double th12 = (double)dihedral(O, p2, p3, x), th13 = (double)dihedral(O, p3, p2, x);
     double th1x = (double)dihedral(O, x, p2, p3);
     return 2.0 * (3.14159265358979323846 * R1 * R1 - R1 * (t12 * th12 + t13 * th13) - R1 * R1 * th1x);
