@@ -36,10 +36,11 @@ constexpr uint8_t NONE = 0xff;
 constexpr int WARPS = 1;         // warps per block: a warp that finishes frees its slot at once
 constexpr int MINB = 32;         // resident blocks per SM the register budget is sized for
 
-// kernel phases: the whole computation in one kernel, or the cell construction (gather,
-// sort, clipping) and the classification + terms + gradient as two kernels that pass the
-// cell through a global record per atom (each kernel's code then fits the instruction cache)
-enum { PH_ALL = 0, PH_CELL = 1, PH_TERMS = 2 };
+// kernel phases: the whole computation in one kernel, or three kernels that pass the cell
+// through a global record per atom: the cell construction (gather, sort, clipping), the
+// classification (Steps 2a-2c: which simplices of the cell are in C), and the area terms and
+// gradient.  Each kernel's code then fits the instruction cache.
+enum { PH_ALL = 0, PH_CELL = 1, PH_CLASS = 2, PH_TERMS = 3 };
 enum { CELL_OK = 0, CELL_DONE = 1 };   // record flag: CELL_DONE = outputs already written
 
 // Per-warp cell storage.  NE plane entries (0..5 ghosts, then the candidates in sorted
@@ -78,6 +79,10 @@ template <class R, int NE, int NT> struct CellRec {
     uchar4 tv[NT];
     uchar4 ta[NT];
     uint8_t start[NE];
+    uint8_t kf[NT];       // classification (the Smem fields of the same names)
+    uint8_t tf[NT];
+    uint8_t eflag[NE];
+    int iK, icl;
     int nc, hw, flag, pad;
 };
 
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
         const FA<R> wi = {Rr * Rr, Rr * Rr};
         CellRec<R, NE, NT>* rec = (CellRec<R, NE, NT>*)A.cells + s;
         auto done = [&]() {   // the outputs of this atom are written: tell the terms kernel
-            if (PH == PH_CELL && lane == 0) rec->flag = CELL_DONE;
+            if ((PH == PH_CELL || PH == PH_CLASS) && lane == 0) rec->flag = CELL_DONE;
         };
 
         int nc = 0;
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
             for (int k = 0; k < 4; ++k) { V[r][k] = q.v[k]; Va[r][k] = q.a[k]; }
         };
 
-        if constexpr (PH != PH_TERMS) {
+        if constexpr (PH == PH_ALL || PH == PH_CELL) {
         // ---------------- neighbour candidates: balls that may overlap B_i
         {
             int cx = min(max((int)floorf((fi.x - G.lo[0]) * G.inv_cell), 0), G.dims[0] - 1);
@@ -664,19 +669,34 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
                 S->tv[t] = t < hw ? rec->tv[t] : make_uchar4(NONE, NONE, NONE, 0);
                 S->ta[t] = t < hw ? rec->ta[t] : make_uchar4(NONE, NONE, NONE, 0);
             }
+            if constexpr (PH == PH_TERMS) {
+                for (int e = lane; e < np; e += 32) S->eflag[e] = rec->eflag[e];
+                for (int t = lane; t < 32 * nrounds; t += 32) {
+                    S->kf[t] = t < hw ? rec->kf[t] : 0;
+                    S->tf[t] = t < hw ? rec->tf[t] : 0;
+                }
+            }
             if (lane == 0) { S->hw = hw; S->bad = 0; }
             __syncwarp();
 #pragma unroll
             for (int r = 0; r < SPL; ++r) {
                 if (r >= nrounds) break;
                 int t = r * 32 + lane;
-                if (S->tv[t].x != NONE) { compute_vertex(r, t); alive |= 1u << r; }
+                if (S->tv[t].x != NONE) {
+                    if constexpr (PH == PH_CLASS) compute_vertex(r, t);
+                    alive |= 1u << r;
+                }
             }
             __syncwarp();
         }
 
         // ---------------- Step 2a: tetrahedra of C (cell vertices inside B_i)
         unsigned kmask = 0;
+        if constexpr (PH == PH_TERMS) {
+#pragma unroll
+            for (int r = 0; r < SPL; ++r)
+                if ((alive >> r & 1) && S->kf[r * 32 + lane] == 1) kmask |= 1u << r;
+        } else {
 #pragma unroll
         for (int r = 0; r < SPL; ++r) {
             if (r >= nrounds) break;
@@ -729,6 +749,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
             }
         }
         __syncwarp();
+        }
 
         // ---------------- Step 2c / 3: faces (edges of C), area terms, gradient gathers
         // Vectors, angles and the gradient are evaluated in R (float in the mixed mode).  The
@@ -742,6 +763,33 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
         const double wi_w = A.w ? A.w[i] : 1.0;
         const R wif = (R)wi_w;
         int myEK = 0;
+        // edge term of A_i and its gradient gathers, for an edge (i, a) of C that is not closed;
+        // phi_sum and gsum sum the dihedral angles (and their d/dp_i) of its tetrahedra
+        auto edge_term = [&](int a, const P3<R>& pa, R phi_sum, const P3<R>& gsum) {
+            // edge term of A_i (Eqs. phiedge, edge): - Phi_ia S_ia^(i) with
+            // S_ia^(i) = 2 pi R_i h_i and Phi_ia = 1 - sum(theta) / 2 pi, i.e.
+            // R_i h_i (sum(theta) - 2 pi); h_i = (R_i + R_a - d)(R_a - R_i + d) / 2d
+            int ga = S->pg[a];
+            const double Ra = A.R[ga];
+            const R dr = norm3(pa), inv2d = (R)0.5 / dr;
+            const double d = (double)dr;
+            const double hi = ((c.Ri + Ra) - d) * ((Ra - c.Ri) + d) * (double)inv2d;
+            area_acc += c.Ri * hi * ((double)phi_sum - TWO_PI);
+            if (GRAD) {
+                const R waf = (R)(A.w ? A.w[ga] : 1.0), Raf = (R)Ra;
+                const R dR2 = (R)((c.Ri - Ra) * (c.Ri + Ra));
+                const R ti = (dr * dr + dR2) * inv2d, ta = (dr * dr - dR2) * inv2d;
+                const R phi = (R)1 - phi_sum * (R)(1.0 / TWO_PI);
+                // vertex + edge parts of the dihedral derivatives around ia (Eq. inexclu)
+                const R kap = -(wif * Rr * ti + waf * Raf * ta);
+                // cap derivatives (Eq. edge): -Phi (2 pi / d)(w_i R_i t_a + w_a R_a t_i) u
+                const R cf = -phi * (R)TWO_PI / (dr * dr) * (wif * Rr * ta + waf * Raf * ti);
+                gx += kap * gsum.x + cf * pa.x;
+                gy += kap * gsum.y + cf * pa.y;
+                gz += kap * gsum.z + cf * pa.z;
+            }
+        };
+        if constexpr (PH != PH_TERMS) {
         for (int a = NG + lane; a < NG + nc; a += 32) {
             uint8_t flag = 0;
             R phi_sum = zero;
@@ -766,11 +814,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
                     if (S->kf[t] == 2) ghost = true;
                     if (S->kf[t] == 1) {
                         ++nk;
-                        P3<R> pb = ppos(S, b), pc = ppos(S, cc);
-                        phi_sum += dihedral_ol(O, pa, pb, pc);
-                        if (GRAD) {
+                        if constexpr (PH == PH_ALL) {
+                            P3<R> pb = ppos(S, b), pc = ppos(S, cc);
+                            phi_sum += dihedral_ol(O, pa, pb, pc);
                             // (i, a, b, c) is positively oriented: (a, b, c) is counter-clockwise
-                            gsum = gsum + dihedral_grad_u_ol(O, pa, pb, pc, (R)1);
+                            if (GRAD) gsum = gsum + dihedral_grad_u_ol(O, pa, pb, pc, (R)1);
                         }
                     }
                     if ((S->tf[t] >> k) & 1) triK = true;
@@ -797,39 +845,47 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
                 if (eK) {
                     flag = 1 | (closed ? 2 : 0);
                     myEK = 1;
-                    if (!closed) {
-                        // edge term of A_i (Eqs. phiedge, edge): - Phi_ia S_ia^(i) with
-                        // S_ia^(i) = 2 pi R_i h_i and Phi_ia = 1 - sum(theta) / 2 pi, i.e.
-                        // R_i h_i (sum(theta) - 2 pi); h_i = (R_i + R_a - d)(R_a - R_i + d) / 2d
-                        int ga = S->pg[a];
-                        const double Ra = A.R[ga];
-                        const R dr = norm3(pa), inv2d = (R)0.5 / dr;
-                        const double d = (double)dr;
-                        const double hi = ((c.Ri + Ra) - d) * ((Ra - c.Ri) + d) * (double)inv2d;
-                        area_acc += c.Ri * hi * ((double)phi_sum - TWO_PI);
-                        if (GRAD) {
-                            const R waf = (R)(A.w ? A.w[ga] : 1.0), Raf = (R)Ra;
-                            const R dR2 = (R)((c.Ri - Ra) * (c.Ri + Ra));
-                            const R ti = (dr * dr + dR2) * inv2d, ta = (dr * dr - dR2) * inv2d;
-                            const R phi = (R)1 - phi_sum * (R)(1.0 / TWO_PI);
-                            // vertex + edge parts of the dihedral derivatives around ia (Eq. inexclu)
-                            const R kap = -(wif * Rr * ti + waf * Raf * ta);
-                            // cap derivatives (Eq. edge): -Phi (2 pi / d)(w_i R_i t_a + w_a R_a t_i) u
-                            const R cf = -phi * (R)TWO_PI / (dr * dr) * (wif * Rr * ta + waf * Raf * ti);
-                            gx += kap * gsum.x + cf * pa.x;
-                            gy += kap * gsum.y + cf * pa.y;
-                            gz += kap * gsum.z + cf * pa.z;
-                        }
-                    }
+                    if constexpr (PH == PH_ALL)
+                        if (!closed) edge_term(a, pa, phi_sum, gsum);
                 }
             }
             S->eflag[a] = flag;
         }
         __syncwarp();
+        } else {
+        // the faces that are edges of C and not closed (classified by the previous kernel)
+        for (int a = NG + lane; a < NG + nc; a += 32) {
+            if ((S->eflag[a] & 3) != 1) continue;
+            const int st = S->start[a] & (NT - 1);
+            const P3<R> O = {zero, zero, zero};
+            const P3<R> pa = ppos(S, a);
+            R phi_sum = zero;
+            P3<R> gsum = {zero, zero, zero};
+            int t = st;
+            for (int step = 0; step < NT; ++step) {
+                uchar4 v = S->tv[t];
+                int k = v.x == a ? 0 : (v.y == a ? 1 : 2);
+                if (S->kf[t] == 1) {
+                    P3<R> pb = ppos(S, tv_get(v, (k + 1) % 3)), pc = ppos(S, tv_get(v, (k + 2) % 3));
+                    phi_sum += dihedral_ol(O, pa, pb, pc);
+                    if (GRAD) gsum = gsum + dihedral_grad_u_ol(O, pa, pb, pc, (R)1);
+                }
+                t = tv_get(S->ta[t], k) & (NT - 1);
+                if (t == st) break;
+            }
+            edge_term(a, pa, phi_sum, gsum);
+        }
+        __syncwarp();
+        }
 
         // vertex i in C?  (an edge of C holds it, or p_i lies in its own cell)
-        bool iK = __any_sync(FULL, myEK);
-        bool icl = true;   // cell entirely inside B_i: interior vertex
+        bool iK, icl;
+        if constexpr (PH == PH_TERMS) {
+            iK = rec->iK != 0;
+            icl = rec->icl != 0;
+        } else {
+        iK = __any_sync(FULL, myEK);
+        icl = true;   // cell entirely inside B_i: interior vertex
 #pragma unroll
         for (int r = 0; r < SPL; ++r)
             if ((alive >> r & 1) && !(kmask >> r & 1)) icl = false;
@@ -847,6 +903,42 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
                 if (sg < 0) ok = false;
             }
             iK = __all_sync(FULL, ok);
+        }
+
+        }
+        if constexpr (PH == PH_CLASS) {
+            __syncwarp();
+            if (S->bad) {
+                if (lane == 0) {
+                    atomicOr(A.status, ST_BADCELL);
+                    A.areas[i] = __longlong_as_double(0x7ff8000000000000ll);
+                    if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
+                }
+                done();
+                __syncwarp();
+                continue;
+            }
+            if (!iK && !EXPORT) {
+                // no simplex of C holds i: A_i = 0 and no gradient gathers
+                if (lane == 0) {
+                    A.areas[i] = 0.0;
+                    if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = 0.0; }
+                }
+                done();
+                __syncwarp();
+                continue;
+            }
+            for (int e = lane; e < NG + nc; e += 32) rec->eflag[e] = S->eflag[e];
+            for (int t = lane; t < S->hw; t += 32) {
+                rec->kf[t] = S->kf[t];
+                rec->tf[t] = (uint8_t)S->tf[t];
+            }
+            if (lane == 0) {
+                rec->iK = iK;
+                rec->icl = icl;
+            }
+            __syncwarp();
+            continue;
         }
 
         // vertex term Omega_i 4 pi R_i^2 (Eq. vertex), Omega_i = 1 - sum of solid angles / 4 pi
@@ -990,8 +1082,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
 }  // namespace
 
 #ifndef DSASA_ATOMS_NO_LAUNCH
-// Fast pass (64 planes, 64 vertex slots) over all atoms: with a cell store, the cell kernel
-// then the terms kernel, else the fused kernel.  The atoms it defers get the fused 128 / 128
+// Fast pass (64 planes, 64 vertex slots) over all atoms: with a cell store, the cell,
+// classification and terms kernels, else the fused kernel.  The atoms it defers get the fused 128 / 128
 // pass, whose grid reads the deferred count from device memory (no host sync).
 template <class R>
 cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
@@ -1011,6 +1103,7 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     const bool g = grad && a.rec == nullptr;
     if (a.cells) {
         k_atoms<R, false, 64, 64, PH_CELL><<<blocks, WARPS * 32, 0, s>>>(fast);
+        k_atoms<R, false, 64, 64, PH_CLASS><<<blocks, WARPS * 32, 0, s>>>(fast);
         if (g) k_atoms<R, true, 64, 64, PH_TERMS><<<blocks, WARPS * 32, 0, s>>>(fast);
         else k_atoms<R, false, 64, 64, PH_TERMS><<<blocks, WARPS * 32, 0, s>>>(fast);
     } else {
