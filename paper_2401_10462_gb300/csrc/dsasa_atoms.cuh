@@ -34,7 +34,8 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int NG = 6;            // ghost planes (the initial cube)
 constexpr uint8_t NONE = 0xff;
 constexpr int WARPS = 1;         // warps per block: a warp that finishes frees its slot at once
-constexpr int MINB = 32;         // resident blocks per SM the register budget is sized for
+// resident blocks per SM that each kernel's register budget is sized for (one warp each)
+constexpr int MINB = 32, MINB_CELL = 32, MINB_CLASS = 32, MINB_TERMS = 32;
 
 // kernel phases: the whole computation in one kernel, or three kernels that pass the cell
 // through a global record per atom: the cell construction (gather, sort, clipping), the
@@ -235,8 +236,11 @@ template <class SM, class R = typename SM::Real> __device__ __forceinline__ P3<R
 }
 
 // ------------------------------------------------------------------ the kernel
+__host__ __device__ constexpr int minb(int ph) {
+    return ph == PH_CELL ? MINB_CELL : (ph == PH_CLASS ? MINB_CLASS : (ph == PH_TERMS ? MINB_TERMS : MINB));
+}
 template <class R, bool GRAD, int NE, int NT, int PH>
-__global__ void __launch_bounds__(WARPS * 32, MINB) k_atoms(AtomArgs A) {
+__global__ void __launch_bounds__(WARPS * 32, minb(PH)) k_atoms(AtomArgs A) {
     constexpr int SPL = NT / 32;      // vertex slots per lane
     constexpr int KMAX = NE - NG;     // overlapping neighbours per atom
     const bool EXPORT = A.rec != nullptr;

@@ -33,7 +33,9 @@ __global__ void k_bbox_init(unsigned* bbox, int n_mol) {
 
 __global__ void k_prep(BuildArgs a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    const bool act = i < a.n;
+    const unsigned mask = __ballot_sync(0xffffffffu, act);
+    if (!act) return;
     int m = 0;
     if (a.offsets) {
         int lo = 0, hi = a.n_mol - 1;   // last m with offsets[m] <= i
@@ -54,14 +56,25 @@ __global__ void k_prep(BuildArgs a) {
     a.molid[i] = m;
     float4 f = make_float4((float)x, (float)y, (float)z, (float)R);
     a.f4[i] = f;
+    // bounding box of the molecule: reduced over the warp first when its atoms share one
+    // molecule (one atomic per warp instead of one per atom on the same 7 words)
+    unsigned lo3[3] = {fenc(f.x), fenc(f.y), fenc(f.z)};
+    unsigned hi4[4] = {lo3[0], lo3[1], lo3[2], fenc(f.w)};
+    const int first = __ffs(mask) - 1;
+    const int m0 = __shfl_sync(mask, m, first);
     unsigned* bb = a.bbox + 8 * m;
-    atomicMin(bb + 0, fenc(f.x));
-    atomicMin(bb + 1, fenc(f.y));
-    atomicMin(bb + 2, fenc(f.z));
-    atomicMax(bb + 3, fenc(f.x));
-    atomicMax(bb + 4, fenc(f.y));
-    atomicMax(bb + 5, fenc(f.z));
-    atomicMax(bb + 6, fenc(f.w));
+    if (__all_sync(mask, m == m0)) {
+        for (int k = 0; k < 3; ++k) lo3[k] = __reduce_min_sync(mask, lo3[k]);
+        for (int k = 0; k < 4; ++k) hi4[k] = __reduce_max_sync(mask, hi4[k]);
+        if ((int)(threadIdx.x & 31) != first) return;
+    }
+    atomicMin(bb + 0, lo3[0]);
+    atomicMin(bb + 1, lo3[1]);
+    atomicMin(bb + 2, lo3[2]);
+    atomicMax(bb + 3, hi4[0]);
+    atomicMax(bb + 4, hi4[1]);
+    atomicMax(bb + 5, hi4[2]);
+    atomicMax(bb + 6, hi4[3]);
 }
 
 // per molecule: cell size and dimensions (cell count stored in base for the scan below)
