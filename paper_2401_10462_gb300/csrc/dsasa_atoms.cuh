@@ -33,9 +33,11 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int NG = 6;            // ghost planes (the initial cube)
 constexpr uint8_t NONE = 0xff;
-constexpr int WARPS = 1;         // warps per block: a warp that finishes frees its slot at once
+// warps per block (a warp that finishes frees its slot at once): fused, cell, classification
+// and terms kernels
+constexpr int WARPS = 1, WARPS_CELL = 2, WARPS_CLASS = 2, WARPS_TERMS = 2;
 // resident blocks per SM that each kernel's register budget is sized for (one warp each)
-constexpr int MINB = 32, MINB_CELL = 32, MINB_CLASS = 32, MINB_TERMS = 32;
+constexpr int MINB = 32, MINB_CELL = 18, MINB_CLASS = 18, MINB_TERMS = 18;
 
 // kernel phases: the whole computation in one kernel, or three kernels that pass the cell
 // through a global record per atom: the cell construction (gather, sort, clipping), the
@@ -239,8 +241,12 @@ template <class SM, class R = typename SM::Real> __device__ __forceinline__ P3<R
 __host__ __device__ constexpr int minb(int ph) {
     return ph == PH_CELL ? MINB_CELL : (ph == PH_CLASS ? MINB_CLASS : (ph == PH_TERMS ? MINB_TERMS : MINB));
 }
+__host__ __device__ constexpr int warps_of(int ph) {
+    return ph == PH_CELL ? WARPS_CELL : (ph == PH_CLASS ? WARPS_CLASS : (ph == PH_TERMS ? WARPS_TERMS : WARPS));
+}
 template <class R, bool GRAD, int NE, int NT, int PH>
-__global__ void __launch_bounds__(WARPS * 32, minb(PH)) k_atoms(AtomArgs A) {
+__global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs A) {
+    constexpr int WARPS = warps_of(PH);
     constexpr int SPL = NT / 32;      // vertex slots per lane
     constexpr int KMAX = NE - NG;     // overlapping neighbours per atom
     const bool EXPORT = A.rec != nullptr;
@@ -1106,10 +1112,11 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     if (a.defer_count) cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
     const bool g = grad && a.rec == nullptr;
     if (a.cells) {
-        k_atoms<R, false, 64, 64, PH_CELL><<<blocks, WARPS * 32, 0, s>>>(fast);
-        k_atoms<R, false, 64, 64, PH_CLASS><<<blocks, WARPS * 32, 0, s>>>(fast);
-        if (g) k_atoms<R, true, 64, 64, PH_TERMS><<<blocks, WARPS * 32, 0, s>>>(fast);
-        else k_atoms<R, false, 64, 64, PH_TERMS><<<blocks, WARPS * 32, 0, s>>>(fast);
+        auto nb = [&](int w) { return (a.n + w - 1) / w; };
+        k_atoms<R, false, 64, 64, PH_CELL><<<nb(WARPS_CELL), WARPS_CELL * 32, 0, s>>>(fast);
+        k_atoms<R, false, 64, 64, PH_CLASS><<<nb(WARPS_CLASS), WARPS_CLASS * 32, 0, s>>>(fast);
+        if (g) k_atoms<R, true, 64, 64, PH_TERMS><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
+        else k_atoms<R, false, 64, 64, PH_TERMS><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
     } else {
         if (g) k_atoms<R, true, 64, 64, PH_ALL><<<blocks, WARPS * 32, 0, s>>>(fast);
         else k_atoms<R, false, 64, 64, PH_ALL><<<blocks, WARPS * 32, 0, s>>>(fast);
