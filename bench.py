@@ -42,6 +42,9 @@ N_ATOMS, SEED = 5000, 0
 # gradient adds 3x the forward term work.
 FLOP_STAR_TET, FLOP_TET, FLOP_EDGE, FLOP_TRI, GRAD_FACTOR = 82.0, 145.0, 15.0, 180.0, 4.0
 STAR_TETS_PER_ATOM = 26.0
+# kernels of one step: cell-list build (bounding box, input pass, grid, grid scan, count, three
+# scan passes, scatter) + cell, classification, terms and large-capacity pass
+LAUNCHES_PER_STEP = 9 + 4
 
 
 def peaks():
@@ -174,6 +177,8 @@ def run_gpu(args):
             for _ in range(warmup):
                 ctx.compute(xyz, rad, a, g)
             ctx.status_sync()
+            # per-kernel CUDA events on the library's stream during the timed steps
+            ctx.set_timing(True)
             evs = []
             for _ in range(steps):
                 flush.zero_()
@@ -186,8 +191,9 @@ def run_gpu(args):
             ctx.status_sync()
         torch.cuda.synchronize(dev)
         ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        ph, calls = ctx.kernel_times()
         ctx.close()
-        return ms, a, g
+        return ms, a, g, {k: v / max(calls, 1) for k, v in ph.items()}
 
     # the dominant kernel, timed alone on the same stream (events around the atom kernel
     # only are not separable from the C ABI call; the cell-list kernels are measured by a
@@ -197,9 +203,9 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
         t_wall0 = time.perf_counter()
-        ms_mixed, a_mix, g_mix = timed("mixed", args.steps, args.warmup)
+        ms_mixed, a_mix, g_mix, ph_mixed = timed("mixed", args.steps, args.warmup)
         t_wall1 = time.perf_counter()
-    ms_fp64, a_64, g_64 = timed("fp64", max(3, args.steps // 2), args.warmup)
+    ms_fp64, a_64, g_64, ph_fp64 = timed("fp64", max(3, args.steps // 2), args.warmup)
     step_ms = sum(ms_mixed) / len(ms_mixed)
     total_s = sum(ms_mixed) / 1e3
     if ws > 1:
@@ -236,8 +242,18 @@ def run_gpu(args):
     ctx.close()
     fl_atom, inc = algorithmic_flops_per_atom(rec, n)
     pk = peaks()
-    achieved = fl_atom * n / (step_ms / 1e3) / 1e12
+    achieved_path = fl_atom * n / (step_ms / 1e3) / 1e12
     traffic = measured_traffic()
+    # the dominant kernel (largest device time per step) and its algorithmic work: the cell
+    # kernel certifies the atom's star (FLOP_STAR_TET per star tetrahedron); the terms
+    # kernel evaluates the area terms and their gradient; the other phases do integer and
+    # topology work only (no term of the flop model)
+    fwd = fl_atom - FLOP_STAR_TET * STAR_TETS_PER_ATOM
+    phase_flop = {"cell": FLOP_STAR_TET * STAR_TETS_PER_ATOM * n, "terms": fwd * n}
+    dom = max(ph_mixed, key=lambda k: ph_mixed[k])
+    dom_ms = ph_mixed[dom]
+    achieved = phase_flop.get(dom, 0.0) / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else 0.0
+    terms_tf = phase_flop["terms"] / (ph_mixed["terms"] / 1e3) / 1e12 if ph_mixed["terms"] > 0 else 0.0
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -246,13 +262,21 @@ def run_gpu(args):
                        fp64_form_atoms_per_s=fp64_value, mixed_over_fp64=value / ws / fp64_value,
                        total_sasa=float(a_mix.sum().item()),
                        fp64_minus_mixed_total_rel=float((a_64.sum() - a_mix.sum()).item() / a_64.sum().item())),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
-                     "frac": achieved / pk["fp32_tflops"], "traffic": traffic,
+        "roofline": {"bound": "alu", "kernel": f"k_atoms phase '{dom}'", "achieved": achieved,
+                     "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
+                     "traffic": traffic, "kernel_ms": dom_ms,
                      "peak_source": "FP32 vector peak derived: 152 SMs x 128 lanes x 2 x max SM clock",
-                     "work_model_flop_per_atom": fl_atom, "complex_incidences_per_atom": inc,
-                     "note": "per-step time of the whole hot path (cell list + atom kernel)"},
+                     "work_model_flop_per_launch": phase_flop.get(dom, 0.0),
+                     "note": "achieved = algorithmic flop of the dominant kernel per launch / its mean "
+                             "CUDA-event duration in the timed region"},
+        "roofline_terms": {"achieved": terms_tf, "frac": terms_tf / pk["fp32_tflops"], "kernel_ms": ph_mixed["terms"],
+                           "work_model_flop_per_launch": phase_flop["terms"]},
+        "roofline_path": {"achieved": achieved_path, "frac": achieved_path / pk["fp32_tflops"],
+                          "work_model_flop_per_atom": fl_atom, "complex_incidences_per_atom": inc,
+                          "note": "whole step (every kernel of the hot path)"},
+        "phase_ms": {"mixed": ph_mixed, "fp64": ph_fp64},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 32 * n},
-        "gpu_launches": 10 * args.steps,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clk.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_serving:

@@ -119,6 +119,20 @@ dsasa_status dsasa_status_sync(dsasa_ctx* ctx);
  * (64 neighbour planes or 64 cell vertices) and were finished by the large-capacity pass. */
 dsasa_status dsasa_deferred_count(dsasa_ctx* ctx, int64_t* deferred);
 
+/* Per-kernel timing (diagnostics, no paper counterpart).  With timing enabled, each compute
+ * call records CUDA events on the context's stream around its kernels; dsasa_kernel_times
+ * synchronises the stream, writes to ms_out[DSASA_NPHASE] the summed device milliseconds per
+ * phase over the calls since the last read (at most 256 calls are recorded) and their number
+ * to *calls_out (may be NULL), and resets the sums.  Phases: */
+#define DSASA_NPHASE 5
+#define DSASA_PHASE_CELL_LIST 0   /* cell-list build (input pass, grid, scan, scatter) */
+#define DSASA_PHASE_CELL 1        /* restricted power cell per atom (gather, sort, clipping) */
+#define DSASA_PHASE_CLASSIFY 2    /* simplices of the cell in C (Steps 2a-2c) */
+#define DSASA_PHASE_TERMS 3       /* area terms and gradient gathers */
+#define DSASA_PHASE_LARGE 4       /* the large-capacity pass over deferred atoms */
+dsasa_status dsasa_set_timing(dsasa_ctx* ctx, int enable);
+dsasa_status dsasa_kernel_times(dsasa_ctx* ctx, double* ms_out, int64_t* calls_out);
+
 /* Diagnostic export of the dual complex C as seen by each atom's local cell.  For every atom
  * i and every simplex of C that contains i, one record of 5 int32 is written to `records`
  * (device, capacity `max_records`): {i, v0, v1, v2, v3} with the simplex's atom indices in

@@ -46,6 +46,8 @@ _lib.dsasa_compute_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_
 _lib.dsasa_compute_host.argtypes = [_vp, _dp, _dp, ctypes.c_double, _i64, _dp, _dp, _dp]
 _lib.dsasa_status_sync.argtypes = [_vp]
 _lib.dsasa_deferred_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+_lib.dsasa_set_timing.argtypes = [_vp, ctypes.c_int]
+_lib.dsasa_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_export_complex.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_last_error.argtypes = [_vp]
 _lib.dsasa_last_error.restype = ctypes.c_char_p
@@ -53,12 +55,13 @@ _lib.dsasa_destroy.argtypes = [_vp]
 _lib.dsasa_version.restype = ctypes.c_char_p
 for _f in ("dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute", "dsasa_compute_vjp",
            "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync", "dsasa_export_complex",
-           "dsasa_deferred_count"):
+           "dsasa_deferred_count", "dsasa_set_timing", "dsasa_kernel_times"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 EXPORTED = ("dsasa_default_config", "dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute",
             "dsasa_compute_vjp", "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync",
-            "dsasa_export_complex", "dsasa_last_error", "dsasa_destroy", "dsasa_version", "dsasa_deferred_count")
+            "dsasa_export_complex", "dsasa_last_error", "dsasa_destroy", "dsasa_version", "dsasa_deferred_count",
+            "dsasa_set_timing", "dsasa_kernel_times")
 
 
 class DSASAError(RuntimeError):
@@ -173,6 +176,19 @@ class Context:
     def status_sync(self):
         """Synchronise and raise if a device-side error was recorded since the last call."""
         self._raise(_lib.dsasa_status_sync(self._h))
+
+    PHASES = ("cell_list", "cell", "classify", "terms", "large")
+
+    def set_timing(self, enable: bool = True):
+        """Record CUDA events around each kernel phase of every compute call (diagnostics)."""
+        self._raise(_lib.dsasa_set_timing(self._h, int(bool(enable))))
+
+    def kernel_times(self):
+        """({phase: summed device ms}, calls) since the last read; resets the sums."""
+        ms = (ctypes.c_double * len(self.PHASES))()
+        calls = ctypes.c_int64(0)
+        self._raise(_lib.dsasa_kernel_times(self._h, ms, ctypes.byref(calls)))
+        return {p: float(ms[k]) for k, p in enumerate(self.PHASES)}, int(calls.value)
 
     def deferred_count(self) -> int:
         """Atoms of the last call whose cell went to the large-capacity pass."""

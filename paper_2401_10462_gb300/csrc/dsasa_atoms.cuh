@@ -525,7 +525,10 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             __syncwarp();
             // boundary edges of the removed region: removed triangle edge (a -> b) whose
             // neighbour is kept; the new face m gets the triangle (a, b, m)
-            uint8_t myb[12];
+            // the plane ids a of this lane's boundary edges, packed in registers (<= 3 per round)
+            unsigned long long apk[(3 * SPL + 7) / 8];
+#pragma unroll
+            for (int w = 0; w < (3 * SPL + 7) / 8; ++w) apk[w] = 0;
             int mynb = 0;
 #pragma unroll
             for (int r = 0; r < SPL; ++r) {
@@ -543,18 +546,27 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                     S->bprev[b] = a;
                     S->bkept[a] = (uint8_t)t2;
                     S->bkedge[a] = (uint8_t)k2;
-                    if (mynb < 12) myb[mynb++] = a; else S->bad = 1;
+#pragma unroll
+                    for (int w = 0; w < (3 * SPL + 7) / 8; ++w)
+                        if ((mynb >> 3) == w) apk[w] |= (unsigned long long)a << (8 * (mynb & 7));
+                    ++mynb;
                 }
             }
-            // count and exclusive prefix of the boundary edges by ballots (<= 3 per slot)
-            int nb = 0, off = 0;
+            auto a_of = [&](int q) -> uint8_t {
+                unsigned long long w = apk[0];
 #pragma unroll
-            for (int j = 0; j < 3 * SPL; ++j) {
-                if (j >= 3 * nrounds) break;
-                unsigned bj = __ballot_sync(FULL, mynb > j);
-                nb += __popc(bj);
-                off += __popc(bj & lanemask_lt());
+                for (int x = 1; x < (3 * SPL + 7) / 8; ++x)
+                    if ((q >> 3) == x) w = apk[x];
+                return (uint8_t)(w >> (8 * (q & 7)));
+            };
+            // count and exclusive prefix of the boundary edges (warp scan)
+            int incl = mynb;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
             }
+            const int nb = __shfl_sync(FULL, incl, 31), off = incl - mynb;
             const int hw = S->hw, nfree = S->nfree;
             const int extra = nb - nrem;
             if (hw + max(0, extra - nfree) > NT) {
@@ -572,11 +584,11 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                     int x = e - nrem;
                     slot = x < nfree ? S->fs[nfree - 1 - x] : hw + (x - nfree);
                 }
-                S->bslot[myb[q]] = (uint8_t)slot;
+                S->bslot[a_of(q)] = (uint8_t)slot;
             }
             __syncwarp();
             for (int q = 0; q < mynb; ++q) {
-                uint8_t a = myb[q];
+                uint8_t a = a_of(q);
                 uint8_t b = S->bnext[a];
                 int sl = S->bslot[a] & (NT - 1);
                 S->tv[sl] = make_uchar4(a, b, (uint8_t)m, 0);
@@ -585,7 +597,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 S->start[a] = (uint8_t)sl;
                 S->rem[sl] = 2;
             }
-            if (mynb > 0 && off == 0) S->start[m] = S->bslot[myb[0]];
+            if (mynb > 0 && off == 0) S->start[m] = S->bslot[a_of(0)];
             __syncwarp();
             // leftover removed slots become free; update the slot allocator
             if (extra < 0) {
@@ -1108,23 +1120,35 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     big.work_list = a.defer_list;
     big.work_count = a.defer_count;
     big.cells = nullptr;
-    int big_blocks = blocks < 4096 ? blocks : 4096;
+    fast.ev = big.ev = nullptr;
+    // the deferred atoms are few: a small grid that loops over them (most calls have none)
+    int big_blocks = blocks < 304 ? blocks : 304;
     if (a.defer_count) cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
     const bool g = grad && a.rec == nullptr;
+    auto mark = [&](int k) {
+        if (a.ev) cudaEventRecord(a.ev[k], s);
+    };
     if (a.cells) {
         auto nb = [&](int w) { return (a.n + w - 1) / w; };
         k_atoms<R, false, 64, 64, PH_CELL><<<nb(WARPS_CELL), WARPS_CELL * 32, 0, s>>>(fast);
+        mark(0);
         k_atoms<R, false, 64, 64, PH_CLASS><<<nb(WARPS_CLASS), WARPS_CLASS * 32, 0, s>>>(fast);
+        mark(1);
         if (g) k_atoms<R, true, 64, 64, PH_TERMS><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
         else k_atoms<R, false, 64, 64, PH_TERMS><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
+        mark(2);
     } else {
         if (g) k_atoms<R, true, 64, 64, PH_ALL><<<blocks, WARPS * 32, 0, s>>>(fast);
         else k_atoms<R, false, 64, 64, PH_ALL><<<blocks, WARPS * 32, 0, s>>>(fast);
+        mark(0);
+        mark(1);
+        mark(2);
     }
     if (a.defer_list) {
         if (g) k_atoms<R, true, 128, 128, PH_ALL><<<big_blocks, WARPS * 32, 0, s>>>(big);
         else k_atoms<R, false, 128, 128, PH_ALL><<<big_blocks, WARPS * 32, 0, s>>>(big);
     }
+    mark(3);
     return cudaGetLastError();
 }
 #endif

@@ -15,6 +15,8 @@
 
 using namespace dsasa;
 
+constexpr int kTimingRing = 256;
+
 struct dsasa_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -40,6 +42,10 @@ struct dsasa_ctx {
     int* defer = nullptr;       // atoms the fast kernel pass defers to the large pass
     unsigned char* cells = nullptr;   // per-atom cell records between the cell and terms kernels
     int* status = nullptr;      // [0] status bits, [1] total cells, [2] deferred count
+    // optional per-kernel timing: events of up to kTimingRing calls since the last read
+    bool timing = false;
+    int n_timed = 0;
+    cudaEvent_t ev[kTimingRing][DSASA_NPHASE + 1] = {};
     unsigned long long* nrec = nullptr;
     // staging for the host-buffer entry point
     int64_t cap_host = 0;
@@ -135,8 +141,11 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     b.R = c->R; b.f4 = c->f4; b.molid = c->molid; b.rank = c->rank; b.cell = c->cell;
     b.bbox = c->bbox; b.grids = c->grids; b.counts = c->counts; b.cstart = c->cstart; b.sidx = c->sidx;
     b.sf4 = c->sf4; b.blocksums = c->blocksums; b.status = c->status; b.ncells_out = c->status + 1;
+    cudaEvent_t* ev = (c->timing && c->n_timed < kTimingRing) ? c->ev[c->n_timed++] : nullptr;
+    if (ev) cudaEventRecord(ev[0], c->stream);
     cudaError_t e = launch_build(b, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cell-list launch");
+    if (ev) cudaEventRecord(ev[1], c->stream);
     AtomArgs a{};
     a.xyz = coords;
     a.R = c->R;
@@ -156,6 +165,7 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     a.defer_list = c->defer;
     a.defer_count = c->status + 2;
     a.cells = c->cells;
+    a.ev = ev ? ev + 2 : nullptr;
     e = c->cfg.precision == DSASA_FP64 ? launch_atoms_f64(a, grad != nullptr, c->stream)
                                        : launch_atoms_f32(a, grad != nullptr, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "atom kernel launch");
@@ -359,10 +369,44 @@ dsasa_status dsasa_export_complex(dsasa_ctx* c, const double* coords, const doub
 
 const char* dsasa_last_error(const dsasa_ctx* c) { return c ? c->err : "null context"; }
 
+dsasa_status dsasa_set_timing(dsasa_ctx* c, int enable) {
+    if (!c) return DSASA_ERR_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess && enable && !c->ev[0][0]) {
+        for (int k = 0; k < kTimingRing && e == cudaSuccess; ++k)
+            for (int j = 0; j <= DSASA_NPHASE && e == cudaSuccess; ++j) e = cudaEventCreate(&c->ev[k][j]);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "timing events");
+    c->timing = enable != 0;
+    c->n_timed = 0;
+    return DSASA_OK;
+}
+
+dsasa_status dsasa_kernel_times(dsasa_ctx* c, double* ms_out, int64_t* calls_out) {
+    if (!c || !ms_out) return DSASA_ERR_ARG;
+    for (int j = 0; j < DSASA_NPHASE; ++j) ms_out[j] = 0.0;
+    if (calls_out) *calls_out = 0;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < c->n_timed && e == cudaSuccess; ++k)
+        for (int j = 0; j < DSASA_NPHASE && e == cudaSuccess; ++j) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, c->ev[k][j], c->ev[k][j + 1]);
+            ms_out[j] += ms;
+        }
+    if (e != cudaSuccess) return cuda_fail(c, e, "timing read");
+    if (calls_out) *calls_out = c->n_timed;
+    c->n_timed = 0;
+    return DSASA_OK;
+}
+
 void dsasa_destroy(dsasa_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    for (int k = 0; k < kTimingRing; ++k)
+        for (int j = 0; j <= DSASA_NPHASE; ++j)
+            if (c->ev[k][j]) cudaEventDestroy(c->ev[k][j]);
     free_scratch(c);
     free_host_staging(c);
     if (c->status) cudaFree(c->status);

@@ -77,21 +77,17 @@ __global__ void k_prep(BuildArgs a) {
     atomicMax(bb + 6, hi4[3]);
 }
 
-// per molecule: cell size and dimensions (cell count stored in base for the scan below)
-__global__ void k_grid_local(BuildArgs a) {
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= a.n_mol) return;
-    const unsigned* bb = a.bbox + 8 * m;
+// Grid of one molecule from its encoded bounding box (bb: min x y z, max x y z, max R) and
+// atom count: cell size and dimensions; the cell count is returned in base.
+__device__ MolGrid make_grid(const unsigned* bb, long long nm, double skin) {
     MolGrid g;
-    long long nm = a.offsets ? (a.offsets[m + 1] - a.offsets[m]) : a.n;
     if (nm <= 0) {
         for (int k = 0; k < 3; ++k) { g.lo[k] = 0.f; g.dims[k] = 1; }
         g.inv_cell = 1.f;
         g.margin = 0.f;
         g.rmax = 0.f;
         g.base = 1;
-        a.grids[m] = g;
-        return;
+        return g;
     }
     float lo[3], hi[3], amax = 0.f;
     for (int k = 0; k < 3; ++k) {
@@ -102,7 +98,7 @@ __global__ void k_grid_local(BuildArgs a) {
     float rmax = fdec(bb[6]);
     // float rounding of coordinates (|x| 2^-24 each), of the difference and of R: slack
     float margin = 1e-5f + 4.0e-7f * (amax + 16.0f);
-    float cell = 2.0f * rmax + (float)a.skin + 2.0f * margin + 1e-3f;
+    float cell = 2.0f * rmax + (float)skin + 2.0f * margin + 1e-3f;
     double cap = 8.0 * (double)nm + 64.0;
     int dims[3];
     for (int it = 0; it < 64; ++it) {
@@ -116,10 +112,18 @@ __global__ void k_grid_local(BuildArgs a) {
     }
     for (int k = 0; k < 3; ++k) { g.lo[k] = lo[k]; g.dims[k] = dims[k]; }
     g.inv_cell = 1.0f / cell;
-    g.margin = margin + 0.5f * (float)a.skin;
+    g.margin = margin + 0.5f * (float)skin;
     g.rmax = rmax;
     g.base = dims[0] * dims[1] * dims[2];
-    a.grids[m] = g;
+    return g;
+}
+
+// per molecule: cell size and dimensions (cell count stored in base for the scan below)
+__global__ void k_grid_local(BuildArgs a) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.n_mol) return;
+    long long nm = a.offsets ? (a.offsets[m + 1] - a.offsets[m]) : a.n;
+    a.grids[m] = make_grid(a.bbox + 8 * m, nm, a.skin);
 }
 
 // exclusive scan of the per-molecule cell counts (one block)
@@ -248,12 +252,101 @@ __global__ void k_scatter(BuildArgs a) {
     a.sf4[pos] = a.f4[i];
 }
 
-}  // namespace
+// The whole build for one molecule of at most kSmallAtoms atoms in one block of 1024 threads
+// (the multi-kernel path's launch overheads dominate at that size).  Same grid, same cells.
+constexpr int kSmallAtoms = 16384, kSmallT = 1024;
+__global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
+    __shared__ unsigned bb[8];
+    __shared__ MolGrid g;
+    __shared__ int ws[kSmallT / 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid < 8) bb[tid] = tid < 3 ? fenc(INFINITY) : (tid < 6 ? fenc(-INFINITY) : (tid == 6 ? fenc(0.0f) : 0u));
+    __syncthreads();
+    unsigned lo[3] = {fenc(INFINITY), fenc(INFINITY), fenc(INFINITY)};
+    unsigned hi[4] = {fenc(-INFINITY), fenc(-INFINITY), fenc(-INFINITY), fenc(0.0f)};
+    for (int i = tid; i < a.n; i += kSmallT) {
+        double x = a.xyz[3 * i], y = a.xyz[3 * i + 1], z = a.xyz[3 * i + 2];
+        double R = a.radii[i] + a.probe;
+        if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(R)) || !(R > 0.0)) {
+            atomicOr(a.status, ST_INPUT);
+            x = y = z = 0.0;
+            R = 1.0;
+        }
+        a.R[i] = R;
+        a.molid[i] = 0;
+        float4 f = make_float4((float)x, (float)y, (float)z, (float)R);
+        a.f4[i] = f;
+        unsigned e[4] = {fenc(f.x), fenc(f.y), fenc(f.z), fenc(f.w)};
+        for (int k = 0; k < 3; ++k) { lo[k] = min(lo[k], e[k]); hi[k] = max(hi[k], e[k]); }
+        hi[3] = max(hi[3], e[3]);
+    }
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = __reduce_min_sync(0xffffffffu, lo[k]);
+        hi[k] = __reduce_max_sync(0xffffffffu, hi[k]);
+    }
+    hi[3] = __reduce_max_sync(0xffffffffu, hi[3]);
+    if (lane == 0) {
+        for (int k = 0; k < 3; ++k) { atomicMin(&bb[k], lo[k]); atomicMax(&bb[3 + k], hi[k]); }
+        atomicMax(&bb[6], hi[3]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        MolGrid gg = make_grid(bb, a.n, a.skin);
+        const int ncells = gg.base;
+        gg.base = 0;
+        g = gg;
+        a.grids[0] = gg;
+        *a.ncells_out = ncells;
+        if (ncells > a.max_cells) atomicOr(a.status, ST_GRID_OVF);
+        for (int k = 0; k < 8; ++k) a.bbox[k] = bb[k];
+    }
+    __syncthreads();
+    const int ncells = min(g.dims[0] * g.dims[1] * g.dims[2], a.max_cells);
+    for (int c = tid; c <= ncells; c += kSmallT) a.counts[c] = 0;
+    __syncthreads();
+    for (int i = tid; i < a.n; i += kSmallT) {
+        int c = cell_of(g, a.f4[i]);
+        if (c >= a.max_cells) c = a.max_cells - 1;   // only after a reported overflow
+        a.cell[i] = c;
+        a.rank[i] = atomicAdd(&a.counts[c], 1);
+    }
+    __syncthreads();
+    // exclusive scan of counts[0 .. ncells] into cstart: each thread scans a contiguous run
+    // of cells, one block scan over the run totals
+    const int per = (ncells + 1 + kSmallT - 1) / kSmallT;
+    const int c0 = min(tid * per, ncells + 1), c1 = min(c0 + per, ncells + 1);
+    int run = 0;
+    for (int c = c0; c < c1; ++c) run += c < ncells ? a.counts[c] : 0;
+    int x = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = ws[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    int pre = (w > 0 ? ws[w - 1] : 0) + x - run;
+    for (int c = c0; c < c1; ++c) {
+        a.cstart[c] = pre;
+        pre += c < ncells ? a.counts[c] : 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < a.n; i += kSmallT) {
+        int pos = a.cstart[a.cell[i]] + a.rank[i];
+        a.sidx[pos] = i;
+        a.sf4[pos] = a.f4[i];
+    }
+}
 
-size_t scan_scratch_ints(int max_cells) { return (size_t)(max_cells + 1 + SCAN_TILE - 1) / SCAN_TILE + 1; }
-
-cudaError_t launch_build(const BuildArgs& a, cudaStream_t s) {
-    if (a.n <= 0) return cudaSuccess;
+cudaError_t launch_build_multi(const BuildArgs& a, cudaStream_t s) {
     const int T = 256;
     int nb = (a.n + T - 1) / T;
     k_bbox_init<<<(a.n_mol + T - 1) / T, T, 0, s>>>(a.bbox, a.n_mol);
@@ -269,6 +362,19 @@ cudaError_t launch_build(const BuildArgs& a, cudaStream_t s) {
     k_scan_down<<<nt, SCAN_T, 0, s>>>(a.counts, len, a.blocksums, a.cstart);
     k_scatter<<<nb, T, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t scan_scratch_ints(int max_cells) { return (size_t)(max_cells + 1 + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+cudaError_t launch_build(const BuildArgs& a, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    if (a.n_mol == 1 && a.n <= kSmallAtoms) {
+        k_build_small<<<1, kSmallT, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    return launch_build_multi(a, s);
 }
 
 }  // namespace dsasa

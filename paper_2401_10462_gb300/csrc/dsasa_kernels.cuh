@@ -80,6 +80,9 @@ struct AtomArgs {
     // per-atom cell records (by sorted position) between the cell kernel and the terms
     // kernel; NULL = one fused kernel
     void* cells;
+    // optional timing: events recorded on the stream after the cell, classification, terms
+    // and large-capacity kernels (NULL = none)
+    cudaEvent_t* ev;
 };
 
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t s);
