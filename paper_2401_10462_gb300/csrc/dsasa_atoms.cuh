@@ -784,6 +784,15 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         R gx = zero, gy = zero, gz = zero;
         const double wi_w = A.w ? A.w[i] : 1.0;
         const R wif = (R)wi_w;
+        // Mixed mode: the radius quantities (R, R^2, R_i -+ R_j, 2 pi) enter as float pairs and
+        // the lane's terms are summed in float-float (no FP64 instruction per term); the
+        // per-atom constants 4 pi R_i^2 and c 2 pi R_i^2 are added once in FP64 at the end.
+        constexpr bool FFM = sizeof(R) == 4;
+        const float2 ri2 = A.Rhl[i];
+        const FF Ri_ff = {ri2.x, ri2.y}, Ri2_ff = ff_mul(Ri_ff, Ri_ff);
+        FF acc_ff = {0.f, 0.f};
+        float cf_sum = 0.f;
+        const float TWO_PI_H = 6.28318548202514648f, TWO_PI_L = -1.74845553e-07f;   // 2 pi = H + L
         int myEK = 0;
         // edge term of A_i and its gradient gathers, for an edge (i, a) of C that is not closed;
         // phi_sum and gsum sum the dihedral angles (and their d/dp_i) of its tetrahedra
@@ -792,14 +801,25 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             // S_ia^(i) = 2 pi R_i h_i and Phi_ia = 1 - sum(theta) / 2 pi, i.e.
             // R_i h_i (sum(theta) - 2 pi); h_i = (R_i + R_a - d)(R_a - R_i + d) / 2d
             int ga = S->pg[a];
-            const double Ra = A.R[ga];
             const R dr = norm3(pa), inv2d = (R)0.5 / dr;
-            const double d = (double)dr;
-            const double hi = ((c.Ri + Ra) - d) * ((Ra - c.Ri) + d) * (double)inv2d;
-            area_acc += c.Ri * hi * ((double)phi_sum - TWO_PI);
+            R Raf, dR2;
+            if constexpr (FFM) {
+                const float2 ra2 = A.Rhl[ga];
+                const FF Ra = {ra2.x, ra2.y}, Sp = ff_add(Ri_ff, Ra), Dm = ff_sub(Ra, Ri_ff);
+                const float hi = ((Sp.h - dr) + Sp.l) * ((Dm.h + dr) + Dm.l) * inv2d;
+                acc_ff = ff_add(acc_ff, ff_mul_f(Ri_ff, hi * ((phi_sum - TWO_PI_H) - TWO_PI_L)));
+                Raf = Ra.h;
+                dR2 = ff_mul(ff_sub(Ri_ff, Ra), Sp).h;
+            } else {
+                const double Ra = A.R[ga];
+                const double d = (double)dr;
+                const double hi = ((c.Ri + Ra) - d) * ((Ra - c.Ri) + d) * (double)inv2d;
+                area_acc += c.Ri * hi * ((double)phi_sum - TWO_PI);
+                Raf = (R)Ra;
+                dR2 = (R)((c.Ri - Ra) * (c.Ri + Ra));
+            }
             if (GRAD) {
-                const R waf = (R)(A.w ? A.w[ga] : 1.0), Raf = (R)Ra;
-                const R dR2 = (R)((c.Ri - Ra) * (c.Ri + Ra));
+                const R waf = (R)(A.w ? A.w[ga] : 1.0);
                 const R ti = (dr * dr + dR2) * inv2d, ta = (dr * dr - dR2) * inv2d;
                 const R phi = (R)1 - phi_sum * (R)(1.0 / TWO_PI);
                 // vertex + edge parts of the dihedral derivatives around ia (Eq. inexclu)
@@ -1006,15 +1026,29 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 uint8_t a = tv_get(v, k), b = tv_get(v, (k + 1) % 3), cc = tv_get(v, (k + 2) % 3);
                 int t2 = tv_get(S->ta[t], k) & (NT - 1);
                 int nk = (S->kf[t] == 1) + (S->kf[t2] == 1);
-                double cf = 1.0 - 0.5 * nk;
+                const R cff = (R)1 - (R)0.5 * (R)nk;
                 P3<R> pa = ppos(S, a), pb = ppos(S, b);
                 int ga = S->pg[a], gb = S->pg[b];
-                double Ra = A.R[ga], Rb = A.R[gb];
-                area_acc += cf * tri_term_mixed_ol(pa, pb, c.Ri, Ra, Rb);
+                R Raf, Rbf, dRab;
+                if constexpr (FFM) {
+                    const float2 ra2 = A.Rhl[ga], rb2 = A.Rhl[gb];
+                    const FF Ra = {ra2.x, ra2.y}, Rb = {rb2.x, rb2.y};
+                    FF v = tri_term_ff_ol(pa, pb, Ri_ff, Ra, Rb, Ri2_ff);
+                    acc_ff = ff_add(acc_ff, FF{cff * v.h, cff * v.l});
+                    cf_sum += cff;
+                    Raf = Ra.h;
+                    Rbf = Rb.h;
+                    dRab = ff_mul(ff_sub(Ra, Rb), ff_add(Ra, Rb)).h;
+                } else {
+                    const double Ra = A.R[ga], Rb = A.R[gb];
+                    area_acc += (double)cff * tri_term_mixed_ol(pa, pb, c.Ri, Ra, Rb);
+                    Raf = (R)Ra;
+                    Rbf = (R)Rb;
+                    dRab = (R)((Ra - Rb) * (Ra + Rb));
+                }
                 if (GRAD) {
                     const P3<R> O = {zero, zero, zero};
                     const R waf = (R)(A.w ? A.w[ga] : 1.0), wbf = (R)(A.w ? A.w[gb] : 1.0);
-                    const R Raf = (R)Ra, Rbf = (R)Rb, cff = (R)cf;
                     // owner i: d/dp_i = -(g2 + g3)
                     P3x2<R> lg = lens_grad_ol(pa, pb, Rr, Raf, Rbf);
                     R sx = -wif * (lg.a.x + lg.b.x), sy = -wif * (lg.a.y + lg.b.y), sz = -wif * (lg.a.z + lg.b.z);
@@ -1033,8 +1067,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                         bool on_t = S->kf[t] == 1;
                         uint8_t x = on_t ? cc : xo;
                         const R dab = norm3(pb - pa), inv2 = (R)0.5 / dab;
-                        const R dR2 = (R)((Ra - Rb) * (Ra + Rb));
-                        const R tab = (dab * dab + dR2) * inv2, tba = (dab * dab - dR2) * inv2;
+                        const R tab = (dab * dab + dRab) * inv2, tba = (dab * dab - dRab) * inv2;
                         const R kap = -(waf * Raf * tab + wbf * Rbf * tba);
                         P3<R> gc = dihedral_grad_c_ol(pa, pb, O, ppos(S, x), on_t ? (R)1 : (R)-1);
                         sx += kap * gc.x; sy += kap * gc.y; sz += kap * gc.z;
@@ -1046,12 +1079,29 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             }
         }
 
-        area_acc = warp_sum_d(area_acc);
         double gxd = 0.0, gyd = 0.0, gzd = 0.0;
-        if (GRAD) {
-            gxd = warp_sum_d((double)gx);
-            gyd = warp_sum_d((double)gy);
-            gzd = warp_sum_d((double)gz);
+        if constexpr (FFM) {
+            area_acc += ff_to_double(acc_ff);
+            area_acc = warp_sum_d(area_acc);
+            for (int o = 16; o > 0; o >>= 1) cf_sum += __shfl_xor_sync(FULL, cf_sum, o);
+            area_acc += (double)cf_sum * TWO_PI * c.Ri * c.Ri;
+            if (GRAD) {
+                for (int o = 16; o > 0; o >>= 1) {
+                    gx += __shfl_xor_sync(FULL, gx, o);
+                    gy += __shfl_xor_sync(FULL, gy, o);
+                    gz += __shfl_xor_sync(FULL, gz, o);
+                }
+                gxd = (double)gx;
+                gyd = (double)gy;
+                gzd = (double)gz;
+            }
+        } else {
+            area_acc = warp_sum_d(area_acc);
+            if (GRAD) {
+                gxd = warp_sum_d((double)gx);
+                gyd = warp_sum_d((double)gy);
+                gzd = warp_sum_d((double)gz);
+            }
         }
         __syncwarp();
         if (lane == 0) {

@@ -27,6 +27,7 @@ struct dsasa_ctx {
     int64_t cap_cells = 0;
     // scratch
     double* R = nullptr;
+    float2* Rhl = nullptr;
     float4* f4 = nullptr;
     int* molid = nullptr;
     int* rank = nullptr;
@@ -82,7 +83,7 @@ template <class T> void dfree(T*& p) {
 }
 
 void free_scratch(dsasa_ctx* c) {
-    dfree(c->R); dfree(c->f4); dfree(c->molid); dfree(c->rank); dfree(c->cell); dfree(c->sidx); dfree(c->sf4);
+    dfree(c->R); dfree(c->Rhl); dfree(c->f4); dfree(c->molid); dfree(c->rank); dfree(c->cell); dfree(c->sidx); dfree(c->sf4);
     dfree(c->bbox); dfree(c->grids); dfree(c->counts); dfree(c->cstart); dfree(c->blocksums); dfree(c->offsets);
     dfree(c->defer); dfree(c->cells);
     c->cap_atoms = c->cap_mol = c->cap_cells = 0;
@@ -114,7 +115,7 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
 #define ALLOC(ptr, count)                                                               \
     e = cudaMalloc((void**)&c->ptr, sizeof(*c->ptr) * (size_t)(count));                 \
     if (e != cudaSuccess) { free_scratch(c); return cuda_fail(c, e, "cudaMalloc " #ptr); }
-    ALLOC(R, na) ALLOC(f4, na) ALLOC(molid, na) ALLOC(rank, na) ALLOC(cell, na) ALLOC(sidx, na) ALLOC(sf4, na)
+    ALLOC(R, na) ALLOC(Rhl, na) ALLOC(f4, na) ALLOC(molid, na) ALLOC(rank, na) ALLOC(cell, na) ALLOC(sidx, na) ALLOC(sf4, na)
     ALLOC(bbox, 8 * nm) ALLOC(grids, nm) ALLOC(counts, nc + 1) ALLOC(cstart, nc + 1) ALLOC(blocksums, nbs)
     ALLOC(offsets, nm + 1) ALLOC(defer, na) ALLOC(cells, na * (int64_t)cell_record_bytes())
 #undef ALLOC
@@ -138,7 +139,7 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     b.offsets = offsets_dev;
     b.skin = c->cfg.skin;
     b.max_cells = (int)c->cap_cells;
-    b.R = c->R; b.f4 = c->f4; b.molid = c->molid; b.rank = c->rank; b.cell = c->cell;
+    b.R = c->R; b.Rhl = c->Rhl; b.f4 = c->f4; b.molid = c->molid; b.rank = c->rank; b.cell = c->cell;
     b.bbox = c->bbox; b.grids = c->grids; b.counts = c->counts; b.cstart = c->cstart; b.sidx = c->sidx;
     b.sf4 = c->sf4; b.blocksums = c->blocksums; b.status = c->status; b.ncells_out = c->status + 1;
     cudaEvent_t* ev = (c->timing && c->n_timed < kTimingRing) ? c->ev[c->n_timed++] : nullptr;
@@ -149,6 +150,7 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     AtomArgs a{};
     a.xyz = coords;
     a.R = c->R;
+    a.Rhl = c->Rhl;
     a.sf4 = c->sf4;
     a.sidx = c->sidx;
     a.molid = c->molid;

@@ -53,6 +53,7 @@ __global__ void k_prep(BuildArgs a) {
         R = 1.0;
     }
     a.R[i] = R;
+    { float h = (float)R; a.Rhl[i] = make_float2(h, (float)(R - (double)h)); }
     a.molid[i] = m;
     float4 f = make_float4((float)x, (float)y, (float)z, (float)R);
     a.f4[i] = f;
@@ -273,6 +274,7 @@ __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
             R = 1.0;
         }
         a.R[i] = R;
+        { float h = (float)R; a.Rhl[i] = make_float2(h, (float)(R - (double)h)); }
         a.molid[i] = 0;
         float4 f = make_float4((float)x, (float)y, (float)z, (float)R);
         a.f4[i] = f;

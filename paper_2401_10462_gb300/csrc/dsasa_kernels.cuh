@@ -39,6 +39,7 @@ struct BuildArgs {
     int max_cells;
     // outputs / scratch
     double* R;         // n
+    float2* Rhl;       // n: R as a float pair (hi, lo), for the float-float area terms
     float4* f4;        // n  (x, y, z, R) float
     int* molid;        // n
     int* rank;         // n
@@ -57,6 +58,7 @@ struct BuildArgs {
 struct AtomArgs {
     const double* xyz;
     const double* R;
+    const float2* Rhl;      // R as (hi, lo) floats
     const float4* sf4;
     const int* sidx;
     const int* molid;

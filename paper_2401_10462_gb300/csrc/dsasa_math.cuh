@@ -498,6 +498,60 @@ template <class T> DS_HD void lens_grad(P3<T> q2, P3<T> q3, T R1, T R2, T R3, P3
     g3 = (n3 * (-be3 * (d3 - t13)) + w3 * st) * ((T)2 * R1 / d3);
 }
 
+// ------------------------------------------------------------------ float-float
+// A value carried as an unevaluated sum h + l of two floats (about 48 significant bits),
+// used to combine the area terms in FP32 without the systematic rounding of quantities that
+// depend only on the radii (R, R^2, R_i +- R_j, pi).  Error-free transformations: Knuth's
+// two-sum and the FMA two-product.
+struct FF { float h, l; };
+DS_HD FF ff_of(double x) {
+    float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+DS_HD void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+DS_HD FF ff_norm(float s, float e) {
+    float h = s + e;
+    return {h, e - (h - s)};
+}
+DS_HD FF ff_add(FF a, FF b) {
+    float s, e;
+    two_sum_f(a.h, b.h, s, e);
+    return ff_norm(s, e + (a.l + b.l));
+}
+DS_HD FF ff_sub(FF a, FF b) { return ff_add(a, FF{-b.h, -b.l}); }
+DS_HD FF ff_mul_f(FF a, float b) {
+    float p = a.h * b;
+    float e = fmaf(a.h, b, -p);
+    return ff_norm(p, fmaf(a.l, b, e));
+}
+DS_HD FF ff_mul(FF a, FF b) {
+    float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    return ff_norm(p, fmaf(a.h, b.l, fmaf(a.l, b.h, e)));
+}
+DS_HD double ff_to_double(FF a) { return (double)a.h + (double)a.l; }
+
+// S_123^(1) - 2 pi R1^2 (Eq. trianglev in the spherical-excess form, p1 at the origin):
+//   -2 R1 (t12 theta_12 + t13 theta_13) - 2 R1^2 theta_1x
+// with the geometry in float and the radius quantities R1, R1^2 and R1^2 - Rk^2 in
+// float-float; the caller adds c 2 pi R1^2 once per atom in FP64.
+DS_HD FF tri_term_ff(P3<float> p2, P3<float> p3, FF R1, FF R2, FF R3, FF R1sq) {
+    const P3<float> O = {0.f, 0.f, 0.f};
+    P3<float> x;
+    triple_point(O, p2, p3, R1.h, R2.h, R3.h, x);
+    const float e12 = norm3(p2), e13 = norm3(p3);
+    const FF w12 = ff_mul(ff_sub(R1, R2), ff_add(R1, R2)), w13 = ff_mul(ff_sub(R1, R3), ff_add(R1, R3));
+    const float t12 = ((e12 * e12 + w12.h) + w12.l) * (0.5f / e12);
+    const float t13 = ((e13 * e13 + w13.h) + w13.l) * (0.5f / e13);
+    const float th12 = dihedral(O, p2, p3, x), th13 = dihedral(O, p3, p2, x), th1x = dihedral(O, x, p2, p3);
+    const float y = t12 * th12 + t13 * th13;
+    return ff_add(ff_mul_f(R1, -2.f * y), ff_mul_f(R1sq, -2.f * th1x));
+}
+
 // ------------------------------------------------------------------ out-of-line forms
 // The kernels call the heavy terms through these (one copy of each body instead of one per
 // call site), which keeps the kernels small enough for the instruction cache.  Results are
@@ -519,6 +573,9 @@ template <class T> DS_HDC P3<T> dihedral_grad_c_ol(P3<T> u, P3<T> v, P3<T> c, P3
 template <class T> DS_HDC T solid_angle_half_ol(P3<T> a, P3<T> b, P3<T> c) { return solid_angle_half(a, b, c); }
 template <class T> DS_HDC double tri_term_mixed_ol(P3<T> p2, P3<T> p3, double R1, double R2, double R3) {
     return tri_term_mixed(p2, p3, R1, R2, R3);
+}
+static DS_HDC FF tri_term_ff_ol(P3<float> p2, P3<float> p3, FF R1, FF R2, FF R3, FF R1sq) {
+    return tri_term_ff(p2, p3, R1, R2, R3, R1sq);
 }
 template <class T> DS_HDC P3x2<T> lens_grad_ol(P3<T> q2, P3<T> q3, T R1, T R2, T R3) {
     P3x2<T> r;

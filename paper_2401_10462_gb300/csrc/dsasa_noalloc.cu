@@ -26,7 +26,8 @@ constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 // byte offsets of the regions inside the static scratch array (each 256-byte aligned)
 constexpr size_t OFF_R = 0;
-constexpr size_t OFF_F4 = al(OFF_R + sizeof(double) * kMaxAtoms);
+constexpr size_t OFF_RHL = al(OFF_R + sizeof(double) * kMaxAtoms);
+constexpr size_t OFF_F4 = al(OFF_RHL + sizeof(float2) * kMaxAtoms);
 constexpr size_t OFF_MOLID = al(OFF_F4 + sizeof(float4) * kMaxAtoms);
 constexpr size_t OFF_RANK = al(OFF_MOLID + sizeof(int) * kMaxAtoms);
 constexpr size_t OFF_CELL = al(OFF_RANK + sizeof(int) * kMaxAtoms);
@@ -85,6 +86,7 @@ extern "C" dsasa_status dsasa_compute_noalloc(const double* coords, const double
     b.skin = 0.0;
     b.max_cells = (int)kMaxCells;
     b.R = (double*)(base + OFF_R);
+    b.Rhl = (float2*)(base + OFF_RHL);
     b.f4 = (float4*)(base + OFF_F4);
     b.molid = (int*)(base + OFF_MOLID);
     b.rank = (int*)(base + OFF_RANK);
@@ -102,6 +104,7 @@ extern "C" dsasa_status dsasa_compute_noalloc(const double* coords, const double
     AtomArgs a{};
     a.xyz = coords;
     a.R = b.R;
+    a.Rhl = b.Rhl;
     a.sf4 = b.sf4;
     a.sidx = b.sidx;
     a.molid = b.molid;

@@ -136,6 +136,20 @@ double mc_tri_mixed(const double* q6, double R1, double R2, double R3, double* g
     return tri_term_mixed(q2, q3, R1, R2, R3);
 }
 
+// the float-float form of S_123^(1) used by the mixed-precision kernel (p1 at the origin)
+double mc_tri_ff(const double* q6, double R1, double R2, double R3) {
+    P3<float> q2 = {(float)q6[0], (float)q6[1], (float)q6[2]}, q3 = {(float)q6[3], (float)q6[4], (float)q6[5]};
+    FF r1 = ff_of(R1);
+    FF v = tri_term_ff(q2, q3, r1, ff_of(R2), ff_of(R3), ff_of(R1 * R1));
+    return ff_to_double(v) + 2.0 * 3.14159265358979323846 * R1 * R1;
+}
+// float-float primitives against double
+double mc_ff_op(int op, double a, double b) {
+    FF x = ff_of(a), y = ff_of(b);
+    FF r = op == 0 ? ff_add(x, y) : (op == 1 ? ff_sub(x, y) : (op == 2 ? ff_mul(x, y) : ff_mul_f(x, (float)b)));
+    return ff_to_double(r);
+}
+
 double mc_dihedral_grad_s(const double* pts, double sg, double* g12) {
     P3<double> p[4], g[4];
     for (int k = 0; k < 4; ++k) p[k] = {pts[3 * k], pts[3 * k + 1], pts[3 * k + 2]};

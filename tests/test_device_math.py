@@ -38,6 +38,10 @@ def mc():
     lib.mc_tri_term.restype = ctypes.c_double
     lib.mc_tri_mixed.argtypes = [dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int]
     lib.mc_tri_mixed.restype = ctypes.c_double
+    lib.mc_tri_ff.argtypes = [dp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.mc_tri_ff.restype = ctypes.c_double
+    lib.mc_ff_op.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lib.mc_ff_op.restype = ctypes.c_double
     lib.mc_dihedral_grad_s.argtypes = [dp, ctypes.c_double, dp]
     lib.mc_dihedral_grad_s.restype = ctypes.c_double
     lib.mc_cap64.argtypes = [ctypes.c_double] * 3
@@ -202,6 +206,40 @@ def test_lens_form_and_closed_gradient_vs_oracle(mc, orc):
         S32 = mc.mc_tri_mixed(_d(q), *R, g32.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1)
         assert abs(S32 - S_ref) < 1e-4
         assert np.abs(g32.reshape(3, 3) - g_ref).max() < 1e-3 * max(1.0, np.abs(g_ref).max())
+
+
+def test_float_float_primitives(mc):
+    """Two-sum / FMA two-product float-float arithmetic: about 2^-44 relative against double."""
+    rng = np.random.default_rng(8)
+    for _ in range(2000):
+        a, b = rng.uniform(-10, 10, 2) * 10.0 ** rng.integers(-3, 3, 2)
+        for op, ref in ((0, a + b), (1, a - b), (2, a * b)):
+            r = mc.mc_ff_op(op, a, b)
+            scale = abs(a) + abs(b) if op < 2 else abs(a * b)
+            assert abs(r - ref) <= 2.0 ** -44 * scale, (op, a, b, r, ref)
+        bf = float(np.float32(b))
+        assert abs(mc.mc_ff_op(3, a, bf) - a * bf) <= 2.0 ** -44 * abs(a * bf)
+
+
+def test_triangle_term_float_float(mc, orc):
+    """The float-float form of Eq. (trianglev) of the mixed kernel against the oracle: the
+    radius quantities carry no float rounding, so the error is that of the float geometry."""
+    rng = np.random.default_rng(9)
+    n, errs = 0, []
+    while n < 300:
+        p = rng.normal(scale=1.8, size=(3, 3))
+        R = rng.choice([2.6, 2.92, 2.95, 3.1, 3.2, 3.3], size=3)
+        S_ref, _ = orc.tri_term(p[0], p[1], p[2], *R)
+        if S_ref is None:
+            continue
+        n += 1
+        q = np.concatenate([p[1] - p[0], p[2] - p[0]])
+        S = mc.mc_tri_ff(_d(q), *R)
+        errs.append(S - S_ref)
+        assert abs(S - S_ref) < 1e-4
+    # no bias beyond the float geometry's scatter
+    errs = np.array(errs)
+    assert abs(errs.mean()) < 4 * errs.std() / np.sqrt(len(errs)) + 1e-7
 
 
 def test_signed_dihedral_gradient_and_cap(mc):
