@@ -61,6 +61,7 @@ template <class R, int NE, int NT> struct Smem {
     uint8_t ord[NE];      // clipping order (entry ids)
     uint8_t eflag[NE];    // face summary: bit0 edge in C, bit1 interior (closed)
     R ephi[NE];           // Phi_ia of the face
+    uint8_t blist[NE];    // boundary edges of the current cut (their first plane id)
     uchar4 tv[NT];        // cell vertex = triangle of plane ids (x = NONE: dead slot)
     uchar4 ta[NT];        // neighbour slots across edges (v0 v1), (v1 v2), (v2 v0)
     uint8_t kf[NT];       // 0 not in C, 1 tetrahedron of C, 2 involves a ghost plane
@@ -510,85 +511,72 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             }
             if (nrem == 0) continue;
             if (nrem == nalive) { empty = true; break; }
-            // removed flags and the ordered list of removed slots
+            // the ordered list of removed slots (round-major)
             int before = 0;
 #pragma unroll
             for (int r = 0; r < SPL; ++r) {
                 if (r >= nrounds) break;
                 int t = r * 32 + lane;
-                if (remv >> r & 1) {
-                    S->rem[t] = 1;
-                    S->rsl[before + __popc(bal[r] & lanemask_lt())] = (uint8_t)t;
-                }
+                if (remv >> r & 1) S->rsl[before + __popc(bal[r] & lanemask_lt())] = (uint8_t)t;
                 before += __popc(bal[r]);
             }
+            auto removed = [&](int t2) -> bool {   // slot t2 removed by this cut (ballot bits)
+                unsigned w = bal[0];
+#pragma unroll
+                for (int r = 1; r < SPL; ++r)
+                    if ((t2 >> 5) == r) w = bal[r];
+                return (w >> (t2 & 31)) & 1u;
+            };
             __syncwarp();
-            // boundary edges of the removed region: removed triangle edge (a -> b) whose
-            // neighbour is kept; the new face m gets the triangle (a, b, m)
-            // the plane ids a of this lane's boundary edges, packed in registers (<= 3 per round)
-            unsigned long long apk[(3 * SPL + 7) / 8];
-#pragma unroll
-            for (int w = 0; w < (3 * SPL + 7) / 8; ++w) apk[w] = 0;
-            int mynb = 0;
-#pragma unroll
-            for (int r = 0; r < SPL; ++r) {
-                if (r >= nrounds) break;
-                if (!(remv >> r & 1)) continue;
-                int t = r * 32 + lane;
-                uchar4 v = S->tv[t], adj = S->ta[t];
-                for (int k = 0; k < 3; ++k) {
-                    int t2 = tv_get(adj, k) & (NT - 1);
-                    if (S->rem[t2]) continue;
-                    uint8_t a = tv_get(v, k) & (NE - 1), b = tv_get(v, (k + 1) % 3) & (NE - 1);
-                    uchar4 adj2 = S->ta[t2];
-                    int k2 = adj2.x == t ? 0 : (adj2.y == t ? 1 : 2);
+            // boundary edges of the removed region, one lane per edge of a removed triangle:
+            // edge (a -> b) whose neighbour is kept; the new face m gets the triangle (a, b, m)
+            // in the slot of boundary edge number e (the e-th removed slot, then free slots)
+            const int hw = S->hw, nfree = S->nfree;
+            int nb = 0;
+            for (int c0 = 0; c0 < 3 * nrem; c0 += 32) {
+                const int e3 = c0 + lane;
+                bool isb = false;
+                uint8_t a = 0, b = 0, t2 = 0, k2 = 0;
+                if (e3 < 3 * nrem) {
+                    const int t = S->rsl[e3 / 3], k = e3 - 3 * (e3 / 3);
+                    const uchar4 v = S->tv[t], adj = S->ta[t];
+                    t2 = tv_get(adj, k) & (NT - 1);
+                    if (!removed(t2)) {
+                        isb = true;
+                        a = tv_get(v, k) & (NE - 1);
+                        b = tv_get(v, (k + 1) % 3) & (NE - 1);
+                        const uchar4 adj2 = S->ta[t2];
+                        k2 = adj2.x == t ? 0 : (adj2.y == t ? 1 : 2);
+                    }
+                }
+                const unsigned bb = __ballot_sync(FULL, isb);
+                if (isb) {
+                    const int e = nb + __popc(bb & lanemask_lt());
+                    int slot;
+                    if (e < nrem) slot = S->rsl[e];
+                    else {
+                        int x = e - nrem;
+                        slot = x < nfree ? S->fs[nfree - 1 - x] : hw + (x - nfree);
+                    }
+                    S->blist[e & (NE - 1)] = a;
                     S->bnext[a] = b;
                     S->bprev[b] = a;
-                    S->bkept[a] = (uint8_t)t2;
-                    S->bkedge[a] = (uint8_t)k2;
-#pragma unroll
-                    for (int w = 0; w < (3 * SPL + 7) / 8; ++w)
-                        if ((mynb >> 3) == w) apk[w] |= (unsigned long long)a << (8 * (mynb & 7));
-                    ++mynb;
+                    S->bkept[a] = t2;
+                    S->bkedge[a] = k2;
+                    S->bslot[a] = (uint8_t)slot;
                 }
+                nb += __popc(bb);
             }
-            auto a_of = [&](int q) -> uint8_t {
-                unsigned long long w = apk[0];
-#pragma unroll
-                for (int x = 1; x < (3 * SPL + 7) / 8; ++x)
-                    if ((q >> 3) == x) w = apk[x];
-                return (uint8_t)(w >> (8 * (q & 7)));
-            };
-            // count and exclusive prefix of the boundary edges (warp scan)
-            int incl = mynb;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int nb = __shfl_sync(FULL, incl, 31), off = incl - mynb;
-            const int hw = S->hw, nfree = S->nfree;
             const int extra = nb - nrem;
-            if (hw + max(0, extra - nfree) > NT) {
+            if (hw + max(0, extra - nfree) > NT || nb > NE) {
                 __syncwarp();
                 if (lane == 0) S->bad = 2;
                 __syncwarp();
                 break;
             }
             __syncwarp();
-            for (int q = 0; q < mynb; ++q) {
-                int e = off + q;
-                int slot;
-                if (e < nrem) slot = S->rsl[e];
-                else {
-                    int x = e - nrem;
-                    slot = x < nfree ? S->fs[nfree - 1 - x] : hw + (x - nfree);
-                }
-                S->bslot[a_of(q)] = (uint8_t)slot;
-            }
-            __syncwarp();
-            for (int q = 0; q < mynb; ++q) {
-                uint8_t a = a_of(q);
+            for (int e = lane; e < nb; e += 32) {
+                uint8_t a = S->blist[e];
                 uint8_t b = S->bnext[a];
                 int sl = S->bslot[a] & (NT - 1);
                 S->tv[sl] = make_uchar4(a, b, (uint8_t)m, 0);
@@ -597,7 +585,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 S->start[a] = (uint8_t)sl;
                 S->rem[sl] = 2;
             }
-            if (mynb > 0 && off == 0) S->start[m] = S->bslot[a_of(0)];
+            if (lane == 0) S->start[m] = S->bslot[S->blist[0]];
             __syncwarp();
             // leftover removed slots become free; update the slot allocator
             if (extra < 0) {
@@ -619,10 +607,13 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             for (int r = 0; r < SPL; ++r) {
                 if (r >= nrounds) break;
                 int t = r * 32 + lane;
-                uint8_t st = S->rem[t];
-                if (st == 2) { compute_vertex(r, t); alive |= 1u << r; }
-                else if (st == 1) alive &= ~(1u << r);
-                if (st) S->rem[t] = 0;
+                if (S->rem[t] == 2) {
+                    compute_vertex(r, t);
+                    alive |= 1u << r;
+                    S->rem[t] = 0;
+                } else if (remv >> r & 1) {
+                    alive &= ~(1u << r);
+                }
             }
             __syncwarp();
         }
