@@ -288,6 +288,7 @@ struct Result {
     int n = 0;
     Geo g;
     std::vector<std::array<int, 4>> rt_tets;      // tetrahedra with 4 atoms (sorted)
+    std::vector<std::array<int, 4>> all_tets;     // every tetrahedron (far points n..n+3 too)
     long rt_tets_total = 0;                        // including the ones with far points
     std::vector<char> redundant;
     // the dual complex C (sorted index tuples)
@@ -398,6 +399,7 @@ static void build(Result& res, int n, const double* xyz, const double* radii, do
     std::vector<std::array<int, 4>> alive_tets;
     for (size_t t = 0; t < rt.T.size(); ++t)
         if (rt.alive[t]) alive_tets.push_back({rt.T[t].v[0], rt.T[t].v[1], rt.T[t].v[2], rt.T[t].v[3]});
+    res.all_tets = alive_tets;
     std::map<std::array<int, 4>, int> tet_id;
     std::vector<char> tetK;
     for (auto& a : res.rt_tets) {
@@ -795,6 +797,148 @@ static int gb_sphere(int i, int n, const double* xyz, const double* radii, doubl
 // ------------------------------------------------------------------ C ABI for ctypes
 using namespace oracle;
 
+// ---------------------------------------------------------------- molecular volume
+// Per-atom volume V_i = vol(B_i cap L_i) (the power-cell partition of the union of balls,
+// Sum_i V_i = vol(union B)).  By the divergence theorem over the closed surface
+// boundary(B_i cap L_i), with the origin at p_i:
+//   V_i = (1/3) [ R_i A_i + Sum_j h_ij a_ij ],
+// where A_i is the exposed sphere area (the SASA of atom i), a_ij the area of the power-
+// diagram face L_i cap L_j inside B_i, and h_ij = b_j / |q_j| the signed distance of that
+// face's plane from p_i.  The vector area of a closed surface is zero, so the exposed
+// sphere piece has vector area -Sum_j a_ij u_ij (u_ij the unit normal towards j), which is
+// d vol(union B) / d p_i (moving sphere i by dp sweeps its exposed piece).
+//
+// Here the face polygon of the edge ij is the ring of power centres of the triangulation's
+// tetrahedra around ij (far points included), and a_ij the area of its intersection with
+// the disk B_i cap plane, summed over the fan of triangles from the disk centre.
+
+// signed area of the triangle (0, a, b) intersected with the disk |x| <= r (2-D)
+static double tri_disk_area(double ax, double ay, double bx, double by, double r) {
+    auto cross = [](double ux, double uy, double vx, double vy) { return ux * vy - uy * vx; };
+    auto sector = [&](double ux, double uy, double vx, double vy) {
+        return 0.5 * r * r * std::atan2(cross(ux, uy, vx, vy), ux * vx + uy * vy);
+    };
+    const double r2 = r * r;
+    const double aa = ax * ax + ay * ay, bb = bx * bx + by * by;
+    const bool ain = aa <= r2, bin = bb <= r2;
+    if (ain && bin) return 0.5 * cross(ax, ay, bx, by);
+    // points a + t (b - a) on the circle: |a|^2 + 2 t a.d + t^2 |d|^2 = r^2
+    const double dx = bx - ax, dy = by - ay;
+    const double A = dx * dx + dy * dy, B = ax * dx + ay * dy, C = aa - r2;
+    const double disc = B * B - A * C;
+    if (ain) {   // leaves the disk at t1 in [0, 1]
+        double t1 = (-B + std::sqrt(std::max(disc, 0.0))) / A;
+        double px = ax + t1 * dx, py = ay + t1 * dy;
+        return 0.5 * cross(ax, ay, px, py) + sector(px, py, bx, by);
+    }
+    if (bin) {   // enters at t0 in [0, 1]
+        double t0 = (-B - std::sqrt(std::max(disc, 0.0))) / A;
+        double px = ax + t0 * dx, py = ay + t0 * dy;
+        return sector(ax, ay, px, py) + 0.5 * cross(px, py, bx, by);
+    }
+    if (A > 0 && disc > 0) {
+        double sq = std::sqrt(disc), t0 = (-B - sq) / A, t1 = (-B + sq) / A;
+        if (t0 > 0 && t1 < 1) {
+            double px = ax + t0 * dx, py = ay + t0 * dy, qx = ax + t1 * dx, qy = ay + t1 * dy;
+            return sector(ax, ay, px, py) + 0.5 * cross(px, py, qx, qy) + sector(qx, qy, bx, by);
+        }
+    }
+    return sector(ax, ay, bx, by);
+}
+
+static void compute_volumes(const Result& res, const std::vector<long double>& A, std::vector<double>& vol,
+                            std::vector<double>& grad) {
+    const Geo& g = res.g;
+    const int n = res.n;
+    vol.assign(n, 0.0);
+    grad.assign(3 * n, 0.0);
+    // link of every edge of C: for each tetrahedron around ij the two other vertices
+    std::map<std::array<int, 2>, std::vector<std::array<int, 2>>> ring;
+    std::set<std::array<int, 2>> inC(res.ke.begin(), res.ke.end());
+    for (auto& v : res.all_tets)
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b) {
+                std::array<int, 2> e = {std::min(v[a], v[b]), std::max(v[a], v[b])};
+                if (!inC.count(e)) continue;
+                std::array<int, 2> o;
+                int m = 0;
+                for (int c = 0; c < 4; ++c) if (c != a && c != b) o[m++] = v[c];
+                ring[e].push_back(o);
+            }
+    // power centre of the tetrahedron (own, j, k, l) relative to p_own: q_m . z = b_m
+    auto plane = [&](int own, int m, double q[3], double& b) {
+        const Pt &P = g.pts[own], &M = g.pts[m];
+        q[0] = M.x - P.x; q[1] = M.y - P.y; q[2] = M.z - P.z;
+        b = 0.5 * ((q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) - M.R * M.R + P.R * P.R);
+    };
+    auto centre = [&](int own, int j, int k, int l, double z[3]) {
+        double qa[3], qb[3], qc[3], ba, bb, bc;
+        plane(own, j, qa, ba); plane(own, k, qb, bb); plane(own, l, qc, bc);
+        V3 A3 = {qa[0], qa[1], qa[2]}, B3 = {qb[0], qb[1], qb[2]}, C3 = {qc[0], qc[1], qc[2]};
+        V3 bcx = crossv(B3, C3), cax = crossv(C3, A3), abx = crossv(A3, B3);
+        double D = dotv(A3, bcx);
+        V3 Z = (bcx * ba + cax * bb + abx * bc) * (1.0 / D);
+        z[0] = Z.x; z[1] = Z.y; z[2] = Z.z;
+    };
+    for (auto& kv : ring) {
+        const int ei = kv.first[0], ej = kv.first[1];
+        // order the ring: consecutive tetrahedra share one link vertex
+        std::vector<std::array<int, 2>> L = kv.second;
+        std::vector<int> cyc;
+        {
+            std::vector<char> used(L.size(), 0);
+            int cur = 0;
+            used[0] = 1;
+            cyc.push_back(0);
+            int next_v = L[0][1];
+            for (size_t s = 1; s < L.size(); ++s) {
+                int found = -1;
+                for (size_t t = 0; t < L.size(); ++t)
+                    if (!used[t] && (L[t][0] == next_v || L[t][1] == next_v)) { found = (int)t; break; }
+                if (found < 0) break;
+                used[found] = 1;
+                cyc.push_back(found);
+                next_v = L[found][0] == next_v ? L[found][1] : L[found][0];
+                cur = found;
+            }
+            (void)cur;
+        }
+        for (int side = 0; side < 2; ++side) {
+            const int own = side == 0 ? ei : ej, oth = side == 0 ? ej : ei;
+            const double Ri = g.pts[own].R;
+            double q[3], b;
+            plane(own, oth, q, b);
+            const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2], qn = std::sqrt(qq);
+            const double u[3] = {q[0] / qn, q[1] / qn, q[2] / qn};
+            const double h = b / qn;            // signed distance of the face plane from p_own
+            const double rho2 = Ri * Ri - h * h;
+            if (rho2 <= 0) continue;
+            const double c[3] = {u[0] * h, u[1] * h, u[2] * h};
+            // in-plane basis
+            V3 nn = {u[0], u[1], u[2]}, e1, e2;
+            basis(nn, e1, e2);
+            std::vector<std::array<double, 2>> poly;
+            for (int t : cyc) {
+                double z[3];
+                centre(own, oth, L[t][0], L[t][1], z);
+                V3 d = {z[0] - c[0], z[1] - c[1], z[2] - c[2]};
+                poly.push_back({dotv(d, e1), dotv(d, e2)});
+            }
+            double area = 0.0;
+            const double r = std::sqrt(rho2);
+            for (size_t k = 0; k < poly.size(); ++k) {
+                const auto& P0 = poly[k];
+                const auto& P1 = poly[(k + 1) % poly.size()];
+                area += tri_disk_area(P0[0], P0[1], P1[0], P1[1], r);
+            }
+            area = std::fabs(area);
+            vol[own] += h * area / 3.0;
+            for (int k = 0; k < 3; ++k) grad[3 * own + k] -= area * u[k];
+        }
+    }
+    for (int i = 0; i < n; ++i) vol[i] += g.pts[i].R * (double)A[i] / 3.0;
+}
+
 struct OracleHandle {
     Result res;
     std::string err;
@@ -855,6 +999,19 @@ long oracle_areas(const OracleHandle* h, const double* weights, double* areas, d
     for (int i = 0; i < h->res.n; ++i) { areas[i] = (double)a.A[i]; tot += a.A[i]; }
     if (total) *total = (double)tot;
     if (grad) for (int k = 0; k < 3 * h->res.n; ++k) grad[k] = a.G[k];
+    return a.n_tri_bad;
+}
+
+// per-atom volumes vol(B_i cap L_i) [n], d vol(union)/dx [3n] (may be NULL), total volume
+long oracle_volumes(const OracleHandle* h, double* volumes, double* grad, double* total) {
+    Areas a;
+    compute_areas(h->res, nullptr, false, a);
+    std::vector<double> v, g;
+    compute_volumes(h->res, a.A, v, g);
+    long double tot = 0;
+    for (int i = 0; i < h->res.n; ++i) { volumes[i] = v[i]; tot += v[i]; }
+    if (total) *total = (double)tot;
+    if (grad) for (int k = 0; k < 3 * h->res.n; ++k) grad[k] = g[k];
     return a.n_tri_bad;
 }
 

@@ -56,6 +56,8 @@ def _load():
             lib.oracle_redundant.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ubyte)]
             lib.oracle_areas.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
             lib.oracle_areas.restype = ctypes.c_long
+            lib.oracle_volumes.argtypes = [ctypes.c_void_p, dp, dp, dp]
+            lib.oracle_volumes.restype = ctypes.c_long
             lib.oracle_gauss_bonnet.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
             lib.oracle_gauss_bonnet.restype = ctypes.c_int
             lib.oracle_tri_term.argtypes = [dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
@@ -133,6 +135,18 @@ class Oracle:
         if bad:
             raise RuntimeError(f"{bad} triangles of C without a triple point")
         return a[: self.n], tot.value, (g[: self.n] if g is not None else None)
+
+
+    def volumes(self, grad: bool = True):
+        """Per-atom volumes vol(B_i cap L_i), their total (the union volume) and
+        d(total)/dx (n, 3) (None if grad=False)."""
+        v = np.zeros(max(self.n, 1))
+        g = np.zeros((max(self.n, 1), 3)) if grad else None
+        tot = ctypes.c_double(0)
+        bad = self._lib.oracle_volumes(self._h, _d(v), _d(g) if g is not None else None, ctypes.byref(tot))
+        if bad:
+            raise RuntimeError(f"{bad} triangles of C without a triple point")
+        return v[: self.n], tot.value, (g[: self.n] if g is not None else None)
 
 
 def sasa(coords, radii, probe: float = PROBE, weights=None, grad: bool = True):
