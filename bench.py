@@ -215,6 +215,32 @@ def run_gpu(args):
     value = ws * n * args.steps / total_s
     fp64_value = n / (sum(ms_fp64) / len(ms_fp64) / 1e3)
 
+    # molecular volume (per-atom power-cell volumes and d(union volume)/dx) on top of the
+    # areas: same workload, same timing discipline
+    ctx = api.Context(device=local, stream=stream)
+    av = torch.empty(n, dtype=torch.float64, device=dev)
+    vv = torch.empty(n, dtype=torch.float64, device=dev)
+    gvv = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx.compute_volume(xyz, rad, av, vv, vol_grad_out=gvv)
+        ctx.status_sync()
+        vev = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.compute_volume(xyz, rad, av, vv, vol_grad_out=gvv)
+            e1.record(stream)
+            vev.append((e0, e1))
+        ctx.status_sync()
+    torch.cuda.synchronize(dev)
+    vol_ms = sum(e0.elapsed_time(e1) for e0, e1 in vev) / len(vev)
+    volume = {"ms_per_step": vol_ms, "atoms_per_s": n / vol_ms * 1e3, "total_volume_A3": float(vv.sum().item()),
+              "note": "areas + per-atom power-cell volumes + d(union volume)/dx (no area gradient)"}
+    ctx.close()
+
     # e2e through the C ABI with pinned host buffers (copies inside the timed region)
     ctx = api.Context(device=local, stream=stream)
     hx = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
@@ -261,7 +287,8 @@ def run_gpu(args):
         "config": dict(WORKLOAD, n_atoms=n, replicas=ws, l2="flushed before every timed step (256 MiB write)",
                        fp64_form_atoms_per_s=fp64_value, mixed_over_fp64=value / ws / fp64_value,
                        total_sasa=float(a_mix.sum().item()),
-                       fp64_minus_mixed_total_rel=float((a_64.sum() - a_mix.sum()).item() / a_64.sum().item())),
+                       fp64_minus_mixed_total_rel=float((a_64.sum() - a_mix.sum()).item() / a_64.sum().item()),
+                       volume=volume),
         "roofline": {"bound": "alu", "kernel": f"k_atoms phase '{dom}'", "achieved": achieved,
                      "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
                      "traffic": traffic, "kernel_ms": dom_ms,

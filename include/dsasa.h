@@ -89,6 +89,18 @@ dsasa_status dsasa_set_precision(dsasa_ctx* ctx, int precision);
 dsasa_status dsasa_compute(dsasa_ctx* ctx, const double* coords, const double* radii, double probe,
                            int64_t n, double* areas_out, double* grad_out);
 
+/* Molecular volume (an extension the paper names; no equation of the paper defines it):
+ * as dsasa_compute, and also volumes_out[i] = vol(B_i cap L_i), the part of the probe-
+ * inflated ball of atom i in its power (Laguerre) cell, so that sum_i volumes_out[i] is the
+ * volume of the union of the balls (the solvent-accessible volume); and, if vol_grad_out !=
+ * NULL, vol_grad_out[j] = d(sum_i V_i)/d(p_j) (double[n][3]).  Computed from the same cell
+ * by the divergence theorem: V_i = (R_i A_i + sum_j h_ij s_ij) / 3 with s_ij the area of the
+ * cell face ij inside B_i and h_ij its plane's distance from p_i; the gradient is minus the
+ * faces' vector area.  areas_out and volumes_out are required (double[n], device). */
+dsasa_status dsasa_compute_volume(dsasa_ctx* ctx, const double* coords, const double* radii, double probe,
+                                  int64_t n, double* areas_out, double* grad_out, double* volumes_out,
+                                  double* vol_grad_out);
+
 /* As dsasa_compute, with grad_out[j] = d(sum_i w_i A_i)/d(p_j) for area_weights w
  * (double[n], device; NULL means all ones).  This vector-Jacobian product is what
  * reverse-mode differentiation of an energy sum_i gamma_i A_i needs. */

@@ -41,6 +41,7 @@ _lib.dsasa_set_stream.argtypes = [_vp, _vp]
 _lib.dsasa_set_precision.argtypes = [_vp, ctypes.c_int]
 _lib.dsasa_compute.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp]
 _lib.dsasa_compute_vjp.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp, _vp]
+_lib.dsasa_compute_volume.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp, _vp, _vp]
 _lib.dsasa_compute_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _vp, _vp, ctypes.c_double,
                                      _vp, _vp, _vp]
 _lib.dsasa_compute_host.argtypes = [_vp, _dp, _dp, ctypes.c_double, _i64, _dp, _dp, _dp]
@@ -55,13 +56,13 @@ _lib.dsasa_destroy.argtypes = [_vp]
 _lib.dsasa_version.restype = ctypes.c_char_p
 for _f in ("dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute", "dsasa_compute_vjp",
            "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync", "dsasa_export_complex",
-           "dsasa_deferred_count", "dsasa_set_timing", "dsasa_kernel_times"):
+           "dsasa_deferred_count", "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 EXPORTED = ("dsasa_default_config", "dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute",
             "dsasa_compute_vjp", "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync",
             "dsasa_export_complex", "dsasa_last_error", "dsasa_destroy", "dsasa_version", "dsasa_deferred_count",
-            "dsasa_set_timing", "dsasa_kernel_times")
+            "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume")
 
 
 class DSASAError(RuntimeError):
@@ -144,6 +145,23 @@ class Context:
         self._sync_stream()
         self._raise(_lib.dsasa_compute_vjp(self._h, _ptr(coords), _ptr(radii), float(probe), n, _ptr(weights),
                                            _ptr(areas_out), _ptr(grad_out)))
+
+    def compute_volume(self, coords, radii, areas_out, volumes_out, grad_out=None, vol_grad_out=None,
+                       probe: float = PROBE):
+        """dsasa_compute_volume: areas, per-atom power-cell volumes (sum = union volume) and
+        optionally d(area sum)/dx and d(union volume)/dx, on device tensors."""
+        n = int(coords.shape[0])
+        _check_tensor(coords, "coords", n, 3)
+        _check_tensor(radii, "radii", n)
+        _check_tensor(areas_out, "areas_out", n)
+        _check_tensor(volumes_out, "volumes_out", n)
+        if grad_out is not None:
+            _check_tensor(grad_out, "grad_out", n, 3)
+        if vol_grad_out is not None:
+            _check_tensor(vol_grad_out, "vol_grad_out", n, 3)
+        self._sync_stream()
+        self._raise(_lib.dsasa_compute_volume(self._h, _ptr(coords), _ptr(radii), float(probe), n, _ptr(areas_out),
+                                              _ptr(grad_out), _ptr(volumes_out), _ptr(vol_grad_out)))
 
     def compute_batch(self, offsets, coords, radii, areas_out, grad_out=None, weights=None, probe: float = PROBE):
         """dsasa_compute_batch: molecule m owns atoms [offsets[m], offsets[m+1])."""

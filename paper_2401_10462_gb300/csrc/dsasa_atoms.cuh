@@ -43,7 +43,7 @@ constexpr int MINB = 32, MINB_CELL = 18, MINB_CLASS = 18, MINB_TERMS = 18;
 // through a global record per atom: the cell construction (gather, sort, clipping), the
 // classification (Steps 2a-2c: which simplices of the cell are in C), and the area terms and
 // gradient.  Each kernel's code then fits the instruction cache.
-enum { PH_ALL = 0, PH_CELL = 1, PH_CLASS = 2, PH_TERMS = 3 };
+enum { PH_ALL = 0, PH_CELL = 1, PH_CLASS = 2, PH_TERMS = 3, PH_VOL = 4 };
 enum { CELL_OK = 0, CELL_DONE = 1 };   // record flag: CELL_DONE = outputs already written
 
 // Per-warp cell storage.  NE plane entries (0..5 ghosts, then the candidates in sorted
@@ -202,6 +202,76 @@ template <class SM, class R = typename SM::Real> __device__ __noinline__ VtxFA<R
     vertex_hom(Pa, Pb, Pc, Dv, D);
     return {{Dv.x.v, Dv.y.v, Dv.z.v, D.v}, {Dv.x.a, Dv.y.a, Dv.z.a, D.a}};
 }
+// Volume pieces of the restricted cell (molecular volume, the paper's named extension).  For
+// every face f of the cell (plane q_f . z = b_f, unit normal u_f, signed distance h_f from
+// p_i), the polygon is split by the fan from the centre of the disk B_i cap plane_f into
+// the area s_f inside the ball and o_f outside it.  By the divergence theorem over the
+// closed surface of B_i cap L_i:  V_i = (R_i A_i + sum_f h_f s_f) / 3.  The exposed sphere
+// piece has vector area -sum_f s_f u_f = d vol(union) / d p_i; since the whole cell's faces
+// have zero vector area, that is +sum_f o_f u_f, which vanishes exactly (no cancellation)
+// when the cell lies inside the ball.  Per lane: partial sums over faces.
+template <class SM, class R = typename SM::Real>
+__device__ void cell_volume_terms(const SM* S, int nc, R Ri, int lane, R& hs, R& nx, R& ny, R& nz) {
+    constexpr int NT = SM::kNT, NE = SM::kNE;
+    hs = nx = ny = nz = (R)0;
+    for (int a = lane; a < NG + nc; a += 32) {
+        const int st0 = S->start[a];
+        if (st0 == NONE) continue;
+        const int st = st0 & (NT - 1);
+        {
+            const uchar4 v = S->tv[st];
+            if (!(v.x == a || v.y == a || v.z == a)) continue;   // face clipped away
+        }
+        const R qx = S->pq[a][0], qy = S->pq[a][1], qz = S->pq[a][2], b = S->pq[a][3];
+        const R inv = (R)1 / ds_sqrt(qx * qx + qy * qy + qz * qz);
+        const R h = b * inv;
+        const R rho2 = Ri * Ri - h * h;
+        const R r = rho2 > (R)0 ? ds_sqrt(rho2) : (R)0;
+        const P3<R> u = {qx * inv, qy * inv, qz * inv};
+        const P3<R> tt = fabs(u.x) < (R)0.6 ? P3<R>{(R)1, (R)0, (R)0} : (fabs(u.y) < (R)0.6 ? P3<R>{(R)0, (R)1, (R)0} : P3<R>{(R)0, (R)0, (R)1});
+        P3<R> e1 = cross3(u, tt);
+        e1 = e1 * ((R)1 / norm3(e1));
+        const P3<R> e2 = cross3(u, e1);
+        int t = st;
+        R fx = 0, fy = 0, px = 0, py = 0, sin_ = 0, sout = 0;
+        auto fan = [&](R ax, R ay, R bx, R by) {
+            const R full = (R)0.5 * (ax * by - ay * bx);
+            if (r > (R)0 && ax * ax + ay * ay <= rho2 && bx * bx + by * by <= rho2) {
+                sin_ += full;   // wholly inside: nothing outside
+            } else {
+                const R in = r > (R)0 ? tri_disk_area_ol(ax, ay, bx, by, r) : (R)0;
+                sin_ += in;
+                sout += full - in;
+            }
+        };
+        for (int step = 0; step < NT; ++step) {
+            const uchar4 v = S->tv[t];
+            // cell vertex (planes v.x, v.y, v.z): z = Dv / D
+            const P3<R> A3 = ppos(S, v.x), B3 = ppos(S, v.y), C3 = ppos(S, v.z);
+            const R ba = S->pq[v.x & (NE - 1)][3], bb = S->pq[v.y & (NE - 1)][3], bc = S->pq[v.z & (NE - 1)][3];
+            const P3<R> xbc = cross3(B3, C3), xca = cross3(C3, A3), xab = cross3(A3, B3);
+            const R D = dot3(A3, xbc);
+            const P3<R> z = (xbc * ba + xca * bb + xab * bc) * ((R)1 / D);
+            const P3<R> d = {z.x - u.x * h, z.y - u.y * h, z.z - u.z * h};
+            const R cx = dot3(d, e1), cy = dot3(d, e2);
+            if (step == 0) { fx = cx; fy = cy; }
+            else fan(px, py, cx, cy);
+            px = cx;
+            py = cy;
+            const int k = v.x == a ? 0 : (v.y == a ? 1 : 2);
+            t = tv_get(S->ta[t], k) & (NT - 1);
+            if (t == st) break;
+        }
+        fan(px, py, fx, fy);
+        // the fan runs around the face the same way for every face of the cell: a common sign
+        const R sg = sin_ + sout < (R)0 ? (R)-1 : (R)1;
+        hs += h * sin_ * sg;
+        nx += sout * sg * u.x;
+        ny += sout * sg * u.y;
+        nz += sout * sg * u.z;
+    }
+}
+
 template <class R> struct Gam;
 template <> struct Gam<float> {
     static constexpr float g = G32, gclip = G32_CLIP, tiny = TINY32;
@@ -240,10 +310,10 @@ template <class SM, class R = typename SM::Real> __device__ __forceinline__ P3<R
 
 // ------------------------------------------------------------------ the kernel
 __host__ __device__ constexpr int minb(int ph) {
-    return ph == PH_CELL ? MINB_CELL : (ph == PH_CLASS ? MINB_CLASS : (ph == PH_TERMS ? MINB_TERMS : MINB));
+    return ph == PH_CELL ? MINB_CELL : (ph == PH_CLASS ? MINB_CLASS : ((ph == PH_TERMS || ph == PH_VOL) ? MINB_TERMS : MINB));
 }
 __host__ __device__ constexpr int warps_of(int ph) {
-    return ph == PH_CELL ? WARPS_CELL : (ph == PH_CLASS ? WARPS_CLASS : (ph == PH_TERMS ? WARPS_TERMS : WARPS));
+    return ph == PH_CELL ? WARPS_CELL : (ph == PH_CLASS ? WARPS_CLASS : ((ph == PH_TERMS || ph == PH_VOL) ? WARPS_TERMS : WARPS));
 }
 template <class R, bool GRAD, int NE, int NT, int PH>
 __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs A) {
@@ -293,6 +363,18 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             for (int k = 0; k < 4; ++k) { V[r][k] = q.v[k]; Va[r][k] = q.a[k]; }
         };
 
+        // molecular volume of the atom from its classified cell (lane 0 writes)
+        auto write_volume = [&](double Ai) {
+            R hs, nx, ny, nz;
+            cell_volume_terms(S, nc, Rr, lane, hs, nx, ny, nz);
+            const double hsum = warp_sum_d((double)hs);
+            const double gx = warp_sum_d((double)nx), gy = warp_sum_d((double)ny), gz = warp_sum_d((double)nz);
+            if (lane == 0) {
+                A.vol[i] = (c.Ri * Ai + hsum) / 3.0;
+                if (A.vgrad) { A.vgrad[3 * i] = gx; A.vgrad[3 * i + 1] = gy; A.vgrad[3 * i + 2] = gz; }
+            }
+        };
+
         if constexpr (PH == PH_ALL || PH == PH_CELL) {
         // ---------------- neighbour candidates: balls that may overlap B_i
         {
@@ -338,6 +420,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 atomicOr(A.status, ST_CAND_OVF);
                 A.areas[i] = __longlong_as_double(0x7ff8000000000000ll);
                 if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
+                if (A.vol) A.vol[i] = __longlong_as_double(0x7ff8000000000000ll);
             }
             done();
             __syncwarp();
@@ -630,6 +713,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 atomicOr(A.status, S->bad == 2 ? ST_TRI_OVF : ST_BADCELL);
                 A.areas[i] = __longlong_as_double(0x7ff8000000000000ll);
                 if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
+                if (A.vol) A.vol[i] = __longlong_as_double(0x7ff8000000000000ll);
             }
             done();
             __syncwarp();
@@ -640,6 +724,8 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             if (lane == 0) {
                 A.areas[i] = 0.0;
                 if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = 0.0; }
+                if (A.vol) A.vol[i] = 0.0;
+                if (A.vgrad) { A.vgrad[3 * i] = A.vgrad[3 * i + 1] = A.vgrad[3 * i + 2] = 0.0; }
             }
             done();
             __syncwarp();
@@ -682,8 +768,9 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 S->tv[t] = t < hw ? rec->tv[t] : make_uchar4(NONE, NONE, NONE, 0);
                 S->ta[t] = t < hw ? rec->ta[t] : make_uchar4(NONE, NONE, NONE, 0);
             }
-            if constexpr (PH == PH_TERMS) {
+            if constexpr (PH == PH_TERMS || PH == PH_VOL)
                 for (int e = lane; e < np; e += 32) S->eflag[e] = rec->eflag[e];
+            if constexpr (PH == PH_TERMS) {
                 for (int t = lane; t < 32 * nrounds; t += 32) {
                     S->kf[t] = t < hw ? rec->kf[t] : 0;
                     S->tf[t] = t < hw ? rec->tf[t] : 0;
@@ -701,6 +788,18 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 }
             }
             __syncwarp();
+            if constexpr (PH == PH_VOL) {
+                if (!(rec->iK)) {
+                    if (lane == 0) {
+                        A.vol[i] = 0.0;
+                        if (A.vgrad) { A.vgrad[3 * i] = A.vgrad[3 * i + 1] = A.vgrad[3 * i + 2] = 0.0; }
+                    }
+                    continue;
+                }
+                write_volume(A.areas[i]);
+                __syncwarp();
+                continue;
+            }
         }
 
         // ---------------- Step 2a: tetrahedra of C (cell vertices inside B_i)
@@ -946,16 +1045,20 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                     atomicOr(A.status, ST_BADCELL);
                     A.areas[i] = __longlong_as_double(0x7ff8000000000000ll);
                     if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
+                    if (A.vol) A.vol[i] = __longlong_as_double(0x7ff8000000000000ll);
+                if (A.vol) A.vol[i] = __longlong_as_double(0x7ff8000000000000ll);
                 }
                 done();
                 __syncwarp();
                 continue;
             }
             if (!iK && !EXPORT) {
-                // no simplex of C holds i: A_i = 0 and no gradient gathers
+                // no simplex of C holds i: A_i = 0 (and V_i = 0) and no gradient gathers
                 if (lane == 0) {
                     A.areas[i] = 0.0;
                     if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = 0.0; }
+                    if (A.vol) A.vol[i] = 0.0;
+                    if (A.vgrad) { A.vgrad[3 * i] = A.vgrad[3 * i + 1] = A.vgrad[3 * i + 2] = 0.0; }
                 }
                 done();
                 __syncwarp();
@@ -1107,6 +1210,15 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 A.grad[3 * i + 2] = iK ? gzd : 0.0;
             }
         }
+        if constexpr (PH == PH_ALL) {
+            if (A.vol) {
+                if (iK) write_volume(area_acc);
+                else if (lane == 0) {
+                    A.vol[i] = 0.0;
+                    if (A.vgrad) { A.vgrad[3 * i] = A.vgrad[3 * i + 1] = A.vgrad[3 * i + 2] = 0.0; }
+                }
+            }
+        }
 
         // ---------------- optional export of the simplices of C containing i
         if (EXPORT) {
@@ -1177,6 +1289,7 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
         mark(1);
         if (g) k_atoms<R, true, 64, 64, PH_TERMS><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
         else k_atoms<R, false, 64, 64, PH_TERMS><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
+        if (a.vol) k_atoms<R, false, 64, 64, PH_VOL><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
         mark(2);
     } else {
         if (g) k_atoms<R, true, 64, 64, PH_ALL><<<blocks, WARPS * 32, 0, s>>>(fast);

@@ -127,7 +127,7 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
 
 dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n, int n_mol,
                  const long long* offsets_dev, const double* w, double* areas, double* grad, int* rec,
-                 int64_t max_rec) {
+                 int64_t max_rec, double* vol = nullptr, double* vgrad = nullptr) {
     dsasa_status st = ensure(c, n, n_mol);
     if (st != DSASA_OK) return st;
     BuildArgs b{};
@@ -159,6 +159,8 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     a.w = w;
     a.areas = areas;
     a.grad = grad;
+    a.vol = vol;
+    a.vgrad = vol ? vgrad : nullptr;
     a.n = (int)n;
     a.status = c->status;
     a.rec = rec;
@@ -254,6 +256,15 @@ dsasa_status dsasa_compute_vjp(dsasa_ctx* c, const double* coords, const double*
 dsasa_status dsasa_compute(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
                            double* areas_out, double* grad_out) {
     return dsasa_compute_vjp(c, coords, radii, probe, n, nullptr, areas_out, grad_out);
+}
+
+dsasa_status dsasa_compute_volume(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
+                                  double* areas_out, double* grad_out, double* volumes_out, double* vol_grad_out) {
+    dsasa_status st = check_common(c, coords, radii, probe, n, areas_out);
+    if (st != DSASA_OK || n == 0) return st;
+    if (!volumes_out) return fail(c, DSASA_ERR_ARG, "volumes_out is NULL");
+    return run(c, coords, radii, probe, n, 1, nullptr, nullptr, areas_out, grad_out, nullptr, 0, volumes_out,
+               vol_grad_out);
 }
 
 dsasa_status dsasa_compute_batch(dsasa_ctx* c, int n_mol, const int64_t* atom_offsets, const double* coords,

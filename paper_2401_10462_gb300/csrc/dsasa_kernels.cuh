@@ -67,6 +67,8 @@ struct AtomArgs {
     const double* w;        // NULL = ones
     double* areas;
     double* grad;           // NULL = no gradient
+    double* vol;            // per-atom volumes vol(B_i cap L_i); NULL = not computed
+    double* vgrad;          // d vol(union) / dx (n x 3); NULL = not computed
     int n;
     int* status;
     // complex export (NULL = off): records {i, v0, v1, v2, v3}

@@ -552,6 +552,40 @@ DS_HD FF tri_term_ff(P3<float> p2, P3<float> p3, FF R1, FF R2, FF R3, FF R1sq) {
     return ff_add(ff_mul_f(R1, -2.f * y), ff_mul_f(R1sq, -2.f * th1x));
 }
 
+// ------------------------------------------------------------------ volume pieces
+// Signed area of the triangle (0, a, b) intersected with the disk |x| <= r in a plane (2-D
+// coordinates): the triangle's part inside the circle is bounded by straight pieces of
+// the side ab and circular sectors where that side runs outside.
+template <class T> DS_HD T tri_disk_area(T ax, T ay, T bx, T by, T r) {
+    const T r2 = r * r;
+    const T aa = ax * ax + ay * ay, bb = bx * bx + by * by;
+    auto crs = [](T ux, T uy, T vx, T vy) { return ux * vy - uy * vx; };
+    auto sector = [&](T ux, T uy, T vx, T vy) { return (T)0.5 * r2 * ds_atan2(crs(ux, uy, vx, vy), ux * vx + uy * vy); };
+    if (aa <= r2 && bb <= r2) return (T)0.5 * crs(ax, ay, bx, by);
+    const T dx = bx - ax, dy = by - ay;
+    const T qa = dx * dx + dy * dy, qb = ax * dx + ay * dy, qc = aa - r2;
+    const T disc = qb * qb - qa * qc;
+    const T sq = disc > (T)0 ? ds_sqrt(disc) : (T)0;
+    if (aa <= r2) {   // a inside: the side leaves the circle at t1
+        const T t1 = (-qb + sq) / qa;
+        const T px = ax + t1 * dx, py = ay + t1 * dy;
+        return (T)0.5 * crs(ax, ay, px, py) + sector(px, py, bx, by);
+    }
+    if (bb <= r2) {   // b inside: the side enters at t0
+        const T t0 = (-qb - sq) / qa;
+        const T px = ax + t0 * dx, py = ay + t0 * dy;
+        return sector(ax, ay, px, py) + (T)0.5 * crs(px, py, bx, by);
+    }
+    if (qa > (T)0 && disc > (T)0) {   // both outside: the side may cross the disk
+        const T t0 = (-qb - sq) / qa, t1 = (-qb + sq) / qa;
+        if (t0 > (T)0 && t1 < (T)1) {
+            const T px = ax + t0 * dx, py = ay + t0 * dy, qx = ax + t1 * dx, qy = ay + t1 * dy;
+            return sector(ax, ay, px, py) + (T)0.5 * crs(px, py, qx, qy) + sector(qx, qy, bx, by);
+        }
+    }
+    return sector(ax, ay, bx, by);
+}
+
 // ------------------------------------------------------------------ out-of-line forms
 // The kernels call the heavy terms through these (one copy of each body instead of one per
 // call site), which keeps the kernels small enough for the instruction cache.  Results are
@@ -577,6 +611,7 @@ template <class T> DS_HDC double tri_term_mixed_ol(P3<T> p2, P3<T> p3, double R1
 static DS_HDC FF tri_term_ff_ol(P3<float> p2, P3<float> p3, FF R1, FF R2, FF R3, FF R1sq) {
     return tri_term_ff(p2, p3, R1, R2, R3, R1sq);
 }
+template <class T> DS_HDC T tri_disk_area_ol(T ax, T ay, T bx, T by, T r) { return tri_disk_area(ax, ay, bx, by, r); }
 template <class T> DS_HDC P3x2<T> lens_grad_ol(P3<T> q2, P3<T> q3, T R1, T R2, T R3) {
     P3x2<T> r;
     lens_grad(q2, q3, R1, R2, R3, r.a, r.b);
