@@ -164,7 +164,7 @@ dsasa_status dsasa_export_complex(dsasa_ctx* ctx, const double* coords, const do
  *   - Same inputs and outputs as dsasa_compute (device pointers, caller-owned; grad_out may be
  *     NULL), computed in the DSASA_MIXED precision on `cuda_stream` (a cudaStream_t or NULL)
  *     of the current device; no context is involved.
- *   - Its scratch is one static device array of about 3.9 MB, sized for at most
+ *   - Its scratch is one static device array of about 4.3 MB, sized for at most
  *     DSASA_NOALLOC_MAX_ATOMS atoms and reserved on every GPU that loads the library until
  *     the process exits.  n > DSASA_NOALLOC_MAX_ATOMS returns DSASA_ERR_CAPACITY and enqueues
  *     nothing; n = 0 returns DSASA_OK.
