@@ -241,6 +241,34 @@ def run_gpu(args):
               "note": "areas + per-atom power-cell volumes + d(union volume)/dx (no area gradient)"}
     ctx.close()
 
+    # Shrake-Rupley numerical SASA (cross-check kernel): 960 points per sphere; every point
+    # is tested against every overlapping neighbour, 9 FP32 operations per test
+    ctx = api.Context(device=local, stream=stream)
+    pts = torch.as_tensor(inputs.sphere_points(960), device=dev)
+    asr = torch.empty(n, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx.compute_sr(xyz, rad, pts, asr)
+        ctx.status_sync()
+        sev = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.compute_sr(xyz, rad, pts, asr)
+            e1.record(stream)
+            sev.append((e0, e1))
+        ctx.status_sync()
+    torch.cuda.synchronize(dev)
+    sr_ms = sum(e0.elapsed_time(e1) for e0, e1 in sev) / len(sev)
+    sr_tf = ctx.sr_tests() * 9.0 / (sr_ms / 1e3) / 1e12
+    shrake_rupley = {"points_per_sphere": 960, "ms_per_call": sr_ms, "atoms_per_s": n / sr_ms * 1e3,
+                     "achieved_tflops": sr_tf, "frac_of_fp32_peak": sr_tf / peaks()["fp32_tflops"],
+                     "total_sasa": float(asr.sum().item()),
+                     "note": "call time includes the cell-list build; 9 FP32 flop per point-neighbour test"}
+    ctx.close()
+
     # e2e through the C ABI with pinned host buffers (copies inside the timed region)
     ctx = api.Context(device=local, stream=stream)
     hx = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
@@ -288,7 +316,7 @@ def run_gpu(args):
                        fp64_form_atoms_per_s=fp64_value, mixed_over_fp64=value / ws / fp64_value,
                        total_sasa=float(a_mix.sum().item()),
                        fp64_minus_mixed_total_rel=float((a_64.sum() - a_mix.sum()).item() / a_64.sum().item()),
-                       volume=volume),
+                       volume=volume, shrake_rupley=shrake_rupley),
         "roofline": {"bound": "alu", "kernel": f"k_atoms phase '{dom}'", "achieved": achieved,
                      "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
                      "traffic": traffic, "kernel_ms": dom_ms,

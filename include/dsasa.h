@@ -101,6 +101,22 @@ dsasa_status dsasa_compute_volume(dsasa_ctx* ctx, const double* coords, const do
                                   int64_t n, double* areas_out, double* grad_out, double* volumes_out,
                                   double* vol_grad_out);
 
+/* Shrake-Rupley numerical SASA, an on-device cross-check of the exact areas (no equation of
+ * the paper; the numerical method of its accuracy comparison): unit_points is float[m][3]
+ * (device, caller-owned) of unit vectors placed on every probe-inflated sphere; a point is
+ * exposed when strictly outside every other ball overlapping the sphere;
+ * areas_out[i] = 4 pi R_i^2 exposed_i / m and, if exposed_out != NULL, exposed_out[i] =
+ * exposed_i (int32[n], device; -1 with a NaN area past 128 overlapping neighbours, reported
+ * as DSASA_ERR_CAPACITY by dsasa_status_sync).  The per-point decision is taken in float32
+ * without contraction: x = R_i s_k, q = float(p_j - p_i), d2 = (dx dx + dy dy) + dz dz,
+ * covered iff d2 <= R_j^2; overlapping means |p_i - p_j|^2 < (R_i + R_j)^2 in float64. */
+dsasa_status dsasa_compute_sr(dsasa_ctx* ctx, const double* coords, const double* radii, double probe,
+                              int64_t n, const float* unit_points, int m, double* areas_out, int32_t* exposed_out);
+
+/* Diagnostics: synchronises and writes the number of point-neighbour tests the last
+ * dsasa_compute_sr call performed (sum over atoms of m x overlapping neighbours). */
+dsasa_status dsasa_sr_tests(dsasa_ctx* ctx, int64_t* tests);
+
 /* As dsasa_compute, with grad_out[j] = d(sum_i w_i A_i)/d(p_j) for area_weights w
  * (double[n], device; NULL means all ones).  This vector-Jacobian product is what
  * reverse-mode differentiation of an energy sum_i gamma_i A_i needs. */

@@ -42,6 +42,8 @@ _lib.dsasa_set_precision.argtypes = [_vp, ctypes.c_int]
 _lib.dsasa_compute.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp]
 _lib.dsasa_compute_vjp.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp, _vp]
 _lib.dsasa_compute_volume.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp, _vp, _vp]
+_lib.dsasa_compute_sr.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, ctypes.c_int, _vp, _vp]
+_lib.dsasa_sr_tests.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_compute_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _vp, _vp, ctypes.c_double,
                                      _vp, _vp, _vp]
 _lib.dsasa_compute_host.argtypes = [_vp, _dp, _dp, ctypes.c_double, _i64, _dp, _dp, _dp]
@@ -56,13 +58,15 @@ _lib.dsasa_destroy.argtypes = [_vp]
 _lib.dsasa_version.restype = ctypes.c_char_p
 for _f in ("dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute", "dsasa_compute_vjp",
            "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync", "dsasa_export_complex",
-           "dsasa_deferred_count", "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume"):
+           "dsasa_deferred_count", "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume", "dsasa_compute_sr",
+           "dsasa_sr_tests"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 EXPORTED = ("dsasa_default_config", "dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute",
             "dsasa_compute_vjp", "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync",
             "dsasa_export_complex", "dsasa_last_error", "dsasa_destroy", "dsasa_version", "dsasa_deferred_count",
-            "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume")
+            "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume",
+            "dsasa_compute_sr", "dsasa_sr_tests")
 
 
 class DSASAError(RuntimeError):
@@ -162,6 +166,28 @@ class Context:
         self._sync_stream()
         self._raise(_lib.dsasa_compute_volume(self._h, _ptr(coords), _ptr(radii), float(probe), n, _ptr(areas_out),
                                               _ptr(grad_out), _ptr(volumes_out), _ptr(vol_grad_out)))
+
+    def compute_sr(self, coords, radii, unit_points, areas_out, exposed_out=None, probe: float = PROBE):
+        """dsasa_compute_sr: Shrake-Rupley areas on the m float32 unit vectors unit_points
+        (device tensor (m, 3)); optional int32 exposed-point counts."""
+        n = int(coords.shape[0])
+        _check_tensor(coords, "coords", n, 3)
+        _check_tensor(radii, "radii", n)
+        _check_tensor(areas_out, "areas_out", n)
+        import torch
+        if unit_points.dtype != torch.float32 or not unit_points.is_cuda or not unit_points.is_contiguous():
+            raise ValueError("unit_points must be a contiguous float32 CUDA tensor (m, 3)")
+        if exposed_out is not None and (exposed_out.dtype != torch.int32 or exposed_out.numel() != n):
+            raise ValueError("exposed_out must be int32 with n entries")
+        self._sync_stream()
+        self._raise(_lib.dsasa_compute_sr(self._h, _ptr(coords), _ptr(radii), float(probe), n, _ptr(unit_points),
+                                          int(unit_points.shape[0]), _ptr(areas_out), _ptr(exposed_out)))
+
+    def sr_tests(self) -> int:
+        """Point-neighbour tests of the last compute_sr call."""
+        t = ctypes.c_int64(0)
+        self._raise(_lib.dsasa_sr_tests(self._h, ctypes.byref(t)))
+        return int(t.value)
 
     def compute_batch(self, offsets, coords, radii, areas_out, grad_out=None, weights=None, probe: float = PROBE):
         """dsasa_compute_batch: molecule m owns atoms [offsets[m], offsets[m+1])."""

@@ -16,7 +16,7 @@ LIB = os.path.join(BUILD, "libdsasa.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
-UNITS = ["dsasa_grid.cu", "dsasa_atoms_f32.cu", "dsasa_atoms_f64.cu", "dsasa_capi.cu", "dsasa_noalloc.cu"]
+UNITS = ["dsasa_grid.cu", "dsasa_atoms_f32.cu", "dsasa_atoms_f64.cu", "dsasa_capi.cu", "dsasa_noalloc.cu", "dsasa_sr.cu"]
 
 
 def nvcc() -> str:

@@ -48,6 +48,7 @@ struct dsasa_ctx {
     int n_timed = 0;
     cudaEvent_t ev[kTimingRing][DSASA_NPHASE + 1] = {};
     unsigned long long* nrec = nullptr;
+    unsigned long long* sr_tests = nullptr;   // Shrake-Rupley point-neighbour tests of the last call
     // staging for the host-buffer entry point
     int64_t cap_host = 0;
     double* h_xyz = nullptr;
@@ -125,11 +126,9 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
     return DSASA_OK;
 }
 
-dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n, int n_mol,
-                 const long long* offsets_dev, const double* w, double* areas, double* grad, int* rec,
-                 int64_t max_rec, double* vol = nullptr, double* vgrad = nullptr) {
-    dsasa_status st = ensure(c, n, n_mol);
-    if (st != DSASA_OK) return st;
+// the cell list of the inputs in the context's scratch (enqueued on its stream)
+cudaError_t build_cells(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n, int n_mol,
+                        const long long* offsets_dev) {
     BuildArgs b{};
     b.xyz = coords;
     b.radii = radii;
@@ -142,12 +141,21 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     b.R = c->R; b.Rhl = c->Rhl; b.f4 = c->f4; b.molid = c->molid; b.rank = c->rank; b.cell = c->cell;
     b.bbox = c->bbox; b.grids = c->grids; b.counts = c->counts; b.cstart = c->cstart; b.sidx = c->sidx;
     b.sf4 = c->sf4; b.blocksums = c->blocksums; b.status = c->status; b.ncells_out = c->status + 1;
+    return launch_build(b, c->stream);
+}
+
+dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n, int n_mol,
+                 const long long* offsets_dev, const double* w, double* areas, double* grad, int* rec,
+                 int64_t max_rec, double* vol = nullptr, double* vgrad = nullptr) {
+    dsasa_status st = ensure(c, n, n_mol);
+    if (st != DSASA_OK) return st;
     cudaEvent_t* ev = (c->timing && c->n_timed < kTimingRing) ? c->ev[c->n_timed++] : nullptr;
     if (ev) cudaEventRecord(ev[0], c->stream);
-    cudaError_t e = launch_build(b, c->stream);
+    cudaError_t e = build_cells(c, coords, radii, probe, n, n_mol, offsets_dev);
     if (e != cudaSuccess) return cuda_fail(c, e, "cell-list launch");
     if (ev) cudaEventRecord(ev[1], c->stream);
     AtomArgs a{};
+
     a.xyz = coords;
     a.R = c->R;
     a.Rhl = c->Rhl;
@@ -217,11 +225,13 @@ dsasa_status dsasa_create(dsasa_ctx** out, int device, void* cuda_stream, const 
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->status, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->nrec, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->sr_tests, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         if (c->status) cudaFree(c->status);
         if (c->nrec) cudaFree(c->nrec);
+        if (c->sr_tests) cudaFree(c->sr_tests);
         delete c;
         return e == cudaErrorMemoryAllocation ? DSASA_ERR_OOM : DSASA_ERR_CUDA;
     }
@@ -265,6 +275,47 @@ dsasa_status dsasa_compute_volume(dsasa_ctx* c, const double* coords, const doub
     if (!volumes_out) return fail(c, DSASA_ERR_ARG, "volumes_out is NULL");
     return run(c, coords, radii, probe, n, 1, nullptr, nullptr, areas_out, grad_out, nullptr, 0, volumes_out,
                vol_grad_out);
+}
+
+dsasa_status dsasa_compute_sr(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
+                              const float* unit_points, int m, double* areas_out, int32_t* exposed_out) {
+    dsasa_status st = check_common(c, coords, radii, probe, n, areas_out);
+    if (st != DSASA_OK || n == 0) return st;
+    if (!unit_points || m <= 0) return fail(c, DSASA_ERR_ARG, "need m > 0 unit points");
+    st = ensure(c, n, 1);
+    if (st != DSASA_OK) return st;
+    cudaError_t e = build_cells(c, coords, radii, probe, n, 1, nullptr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cell-list launch");
+    SRArgs a{};
+    a.xyz = coords;
+    a.R = c->R;
+    a.sf4 = c->sf4;
+    a.sidx = c->sidx;
+    a.molid = c->molid;
+    a.cstart = c->cstart;
+    a.grids = c->grids;
+    a.pts = unit_points;
+    a.m = m;
+    a.n = (int)n;
+    a.areas = areas_out;
+    a.exposed = exposed_out;
+    a.tests = c->sr_tests;
+    a.status = c->status;
+    if (c->sr_tests) cudaMemsetAsync(c->sr_tests, 0, sizeof(unsigned long long), c->stream);
+    e = launch_sr(a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Shrake-Rupley launch");
+    return DSASA_OK;
+}
+
+dsasa_status dsasa_sr_tests(dsasa_ctx* c, int64_t* tests) {
+    if (!c || !tests) return DSASA_ERR_ARG;
+    unsigned long long h = 0;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, c->sr_tests, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "test count read");
+    *tests = (int64_t)h;
+    return DSASA_OK;
 }
 
 dsasa_status dsasa_compute_batch(dsasa_ctx* c, int n_mol, const int64_t* atom_offsets, const double* coords,
@@ -424,6 +475,7 @@ void dsasa_destroy(dsasa_ctx* c) {
     free_host_staging(c);
     if (c->status) cudaFree(c->status);
     if (c->nrec) cudaFree(c->nrec);
+    if (c->sr_tests) cudaFree(c->sr_tests);
     delete c;
 }
 

@@ -89,7 +89,26 @@ struct AtomArgs {
     cudaEvent_t* ev;
 };
 
+// Shrake-Rupley numerical SASA (cross-check): m unit vectors pts[3m] (device)
+struct SRArgs {
+    const double* xyz;
+    const double* R;
+    const float4* sf4;
+    const int* sidx;
+    const int* molid;
+    const int* cstart;
+    const MolGrid* grids;
+    const float* pts;
+    int m;
+    int n;
+    double* areas;
+    int* exposed;                 // NULL = not written
+    unsigned long long* tests;    // NULL = not counted: point-neighbour tests performed
+    int* status;
+};
+
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t s);
+cudaError_t launch_sr(const SRArgs& a, cudaStream_t s);
 cudaError_t launch_atoms_f32(const AtomArgs& a, bool grad, cudaStream_t s);
 cudaError_t launch_atoms_f64(const AtomArgs& a, bool grad, cudaStream_t s);
 size_t scan_scratch_ints(int max_cells);

@@ -165,6 +165,17 @@ def make(kind: str, n: int, seed: int, cache: bool = True) -> Molecule:
     return m
 
 
+def sphere_points(m: int) -> np.ndarray:
+    """m float32 unit vectors on the golden-angle spiral (the point set of the Shrake-Rupley
+    cross-check): z_k = 1 - (2k + 1)/m, phi_k = k pi (3 - sqrt 5), computed in float64 and
+    rounded once."""
+    k = np.arange(m, dtype=np.float64)
+    z = 1.0 - (2.0 * k + 1.0) / m
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = k * np.pi * (3.0 - np.sqrt(5.0))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], 1).astype(np.float32)
+
+
 def poisson_arrivals(count: int, rate_per_s: float, seed: int = 0) -> np.ndarray:
     """Arrival times (s) of a Poisson stream at the given rate."""
     rng = np.random.Generator(np.random.PCG64(seed + 7919))
