@@ -255,11 +255,12 @@ __global__ void k_scatter(BuildArgs a) {
 
 // The whole build for one molecule of at most kSmallAtoms atoms in one block of 1024 threads
 // (the multi-kernel path's launch overheads dominate at that size).  Same grid, same cells.
-constexpr int kSmallAtoms = 16384, kSmallT = 1024;
+constexpr int kSmallAtoms = 16384, kSmallT = 1024, kSmallCells = 8192;
 __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
     __shared__ unsigned bb[8];
     __shared__ MolGrid g;
     __shared__ int ws[kSmallT / 32];
+    __shared__ int scount[kSmallCells];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid < 8) bb[tid] = tid < 3 ? fenc(INFINITY) : (tid < 6 ? fenc(-INFINITY) : (tid == 6 ? fenc(0.0f) : 0u));
     __syncthreads();
@@ -304,21 +305,24 @@ __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
     }
     __syncthreads();
     const int ncells = min(g.dims[0] * g.dims[1] * g.dims[2], a.max_cells);
-    for (int c = tid; c <= ncells; c += kSmallT) a.counts[c] = 0;
+    // counts in shared memory when the grid is small enough (the usual case), else in HBM
+    const bool sm = ncells + 1 <= kSmallCells;
+    int* cnt = sm ? scount : a.counts;
+    for (int c = tid; c <= ncells; c += kSmallT) cnt[c] = 0;
     __syncthreads();
     for (int i = tid; i < a.n; i += kSmallT) {
         int c = cell_of(g, a.f4[i]);
         if (c >= a.max_cells) c = a.max_cells - 1;   // only after a reported overflow
         a.cell[i] = c;
-        a.rank[i] = atomicAdd(&a.counts[c], 1);
+        a.rank[i] = atomicAdd(&cnt[c], 1);
     }
     __syncthreads();
     // exclusive scan of counts[0 .. ncells] into cstart: each thread scans a contiguous run
-    // of cells, one block scan over the run totals
+    // of cells, one block scan over the run totals (the shared copy keeps the starts)
     const int per = (ncells + 1 + kSmallT - 1) / kSmallT;
     const int c0 = min(tid * per, ncells + 1), c1 = min(c0 + per, ncells + 1);
     int run = 0;
-    for (int c = c0; c < c1; ++c) run += c < ncells ? a.counts[c] : 0;
+    for (int c = c0; c < c1; ++c) run += c < ncells ? cnt[c] : 0;
     int x = run;
     for (int o = 1; o < 32; o <<= 1) {
         int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -337,12 +341,14 @@ __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
     __syncthreads();
     int pre = (w > 0 ? ws[w - 1] : 0) + x - run;
     for (int c = c0; c < c1; ++c) {
+        const int v = c < ncells ? cnt[c] : 0;
         a.cstart[c] = pre;
-        pre += c < ncells ? a.counts[c] : 0;
+        if (sm) cnt[c] = pre;
+        pre += v;
     }
     __syncthreads();
     for (int i = tid; i < a.n; i += kSmallT) {
-        int pos = a.cstart[a.cell[i]] + a.rank[i];
+        int pos = (sm ? cnt[a.cell[i]] : a.cstart[a.cell[i]]) + a.rank[i];
         a.sidx[pos] = i;
         a.sf4[pos] = a.f4[i];
     }
