@@ -1275,7 +1275,7 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     big.cells = nullptr;
     fast.ev = big.ev = nullptr;
     // the deferred atoms are few: a small grid that loops over them (most calls have none)
-    int big_blocks = blocks < 304 ? blocks : 304;
+    int big_blocks = blocks < 64 ? blocks : 64;
     if (a.defer_count) cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
     const bool g = grad && a.rec == nullptr;
     auto mark = [&](int k) {

@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
     __syncthreads();
     unsigned lo[3] = {fenc(INFINITY), fenc(INFINITY), fenc(INFINITY)};
     unsigned hi[4] = {fenc(-INFINITY), fenc(-INFINITY), fenc(-INFINITY), fenc(0.0f)};
+#pragma unroll 4
     for (int i = tid; i < a.n; i += kSmallT) {
         double x = a.xyz[3 * i], y = a.xyz[3 * i + 1], z = a.xyz[3 * i + 2];
         double R = a.radii[i] + a.probe;
@@ -310,6 +311,7 @@ __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
     int* cnt = sm ? scount : a.counts;
     for (int c = tid; c <= ncells; c += kSmallT) cnt[c] = 0;
     __syncthreads();
+#pragma unroll 4
     for (int i = tid; i < a.n; i += kSmallT) {
         int c = cell_of(g, a.f4[i]);
         if (c >= a.max_cells) c = a.max_cells - 1;   // only after a reported overflow
@@ -347,6 +349,7 @@ __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
         pre += v;
     }
     __syncthreads();
+#pragma unroll 4
     for (int i = tid; i < a.n; i += kSmallT) {
         int pos = (sm ? cnt[a.cell[i]] : a.cstart[a.cell[i]]) + a.rank[i];
         a.sidx[pos] = i;
