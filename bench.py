@@ -153,6 +153,17 @@ def algorithmic_flops_per_atom(rec, n):
     return FLOP_STAR_TET * STAR_TETS_PER_ATOM + GRAD_FACTOR * fwd, {"tets": tets, "edges": edges, "tris": tris}
 
 
+def replica_throughput(total_s: float, ws: int, n: int, steps: int, device=None) -> float:
+    """Whole-job atoms/s of N independent replicas: every rank timed `steps` steps of `n`
+    atoms in `total_s` seconds; the job takes as long as the slowest rank (max over ranks)."""
+    if ws > 1:
+        import torch
+        t = torch.tensor([total_s], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    return ws * n * steps / total_s
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -195,9 +206,8 @@ def run_gpu(args):
         ctx.close()
         return ms, a, g, {k: v / max(calls, 1) for k, v in ph.items()}
 
-    # the dominant kernel, timed alone on the same stream (events around the atom kernel
-    # only are not separable from the C ABI call; the cell-list kernels are measured by a
-    # separate build-only launch through the same library entry point's components)
+    # timed region: barrier, then K steps with events on the library's stream (per-kernel
+    # events inside the library give the dominant kernel's time)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -207,12 +217,7 @@ def run_gpu(args):
         t_wall1 = time.perf_counter()
     ms_fp64, a_64, g_64, ph_fp64 = timed("fp64", max(3, args.steps // 2), args.warmup)
     step_ms = sum(ms_mixed) / len(ms_mixed)
-    total_s = sum(ms_mixed) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = ws * n * args.steps / total_s
+    value = replica_throughput(sum(ms_mixed) / 1e3, ws, n, args.steps, dev)
     fp64_value = n / (sum(ms_fp64) / len(ms_fp64) / 1e3)
 
     # molecular volume (per-atom power-cell volumes and d(union volume)/dx) on top of the
