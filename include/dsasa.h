@@ -65,7 +65,14 @@ enum { DSASA_MIXED = 0, DSASA_FP64 = 1 };
 
 typedef struct {
     int precision;      /* DSASA_MIXED or DSASA_FP64 */
-    double skin;        /* extra neighbour-search margin in Angstrom (>= 0); 0 = exact overlap */
+    double skin;        /* Verlet skin in Angstrom (>= 0).  0: the cell list is rebuilt every call.
+                         * > 0: single-molecule calls keep per-atom candidate lists (atoms
+                         * within R_i + R_j + skin) on the device and reuse them, without
+                         * rebuilding the cell list, while every atom stays within skin / 2 of
+                         * its position at the last rebuild and n, the radii and the probe are
+                         * unchanged (tested on the device: graph-capturable).  The cells and
+                         * all simplices are recomputed every call; results do not depend on
+                         * reuse beyond rounding. */
     int64_t max_atoms;  /* fixed capacity in atoms, or 0 to grow on demand */
     int64_t max_cells;  /* cap on cell-list cells (0 = default 2^22); larger boxes use coarser cells */
 } dsasa_config;
@@ -112,6 +119,10 @@ dsasa_status dsasa_compute_volume(dsasa_ctx* ctx, const double* coords, const do
  * covered iff d2 <= R_j^2; overlapping means |p_i - p_j|^2 < (R_i + R_j)^2 in float64. */
 dsasa_status dsasa_compute_sr(dsasa_ctx* ctx, const double* coords, const double* radii, double probe,
                               int64_t n, const float* unit_points, int m, double* areas_out, int32_t* exposed_out);
+
+/* Diagnostics: synchronises and writes 1 to *reused if the last call reused the Verlet
+ * lists (skin > 0), else 0. */
+dsasa_status dsasa_lists_reused(dsasa_ctx* ctx, int* reused);
 
 /* Diagnostics: synchronises and writes the number of point-neighbour tests the last
  * dsasa_compute_sr call performed (sum over atoms of m x overlapping neighbours). */

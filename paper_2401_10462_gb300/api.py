@@ -44,6 +44,7 @@ _lib.dsasa_compute_vjp.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _v
 _lib.dsasa_compute_volume.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp, _vp, _vp]
 _lib.dsasa_compute_sr.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, ctypes.c_int, _vp, _vp]
 _lib.dsasa_sr_tests.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+_lib.dsasa_lists_reused.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
 _lib.dsasa_compute_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _vp, _vp, ctypes.c_double,
                                      _vp, _vp, _vp]
 _lib.dsasa_compute_host.argtypes = [_vp, _dp, _dp, ctypes.c_double, _i64, _dp, _dp, _dp]
@@ -59,14 +60,14 @@ _lib.dsasa_version.restype = ctypes.c_char_p
 for _f in ("dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute", "dsasa_compute_vjp",
            "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync", "dsasa_export_complex",
            "dsasa_deferred_count", "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume", "dsasa_compute_sr",
-           "dsasa_sr_tests"):
+           "dsasa_sr_tests", "dsasa_lists_reused"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 EXPORTED = ("dsasa_default_config", "dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute",
             "dsasa_compute_vjp", "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync",
             "dsasa_export_complex", "dsasa_last_error", "dsasa_destroy", "dsasa_version", "dsasa_deferred_count",
             "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume",
-            "dsasa_compute_sr", "dsasa_sr_tests")
+            "dsasa_compute_sr", "dsasa_sr_tests", "dsasa_lists_reused")
 
 
 class DSASAError(RuntimeError):
@@ -182,6 +183,12 @@ class Context:
         self._sync_stream()
         self._raise(_lib.dsasa_compute_sr(self._h, _ptr(coords), _ptr(radii), float(probe), n, _ptr(unit_points),
                                           int(unit_points.shape[0]), _ptr(areas_out), _ptr(exposed_out)))
+
+    def lists_reused(self) -> bool:
+        """Whether the last call reused the Verlet lists (contexts with skin > 0)."""
+        r = ctypes.c_int(0)
+        self._raise(_lib.dsasa_lists_reused(self._h, ctypes.byref(r)))
+        return bool(r.value)
 
     def sr_tests(self) -> int:
         """Point-neighbour tests of the last compute_sr call."""

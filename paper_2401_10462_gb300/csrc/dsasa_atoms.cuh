@@ -376,36 +376,58 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         };
 
         if constexpr (PH == PH_ALL || PH == PH_CELL) {
-        // ---------------- neighbour candidates: balls that may overlap B_i
-        {
-            int cx = min(max((int)floorf((fi.x - G.lo[0]) * G.inv_cell), 0), G.dims[0] - 1);
-            int cy = min(max((int)floorf((fi.y - G.lo[1]) * G.inv_cell), 0), G.dims[1] - 1);
-            int cz = min(max((int)floorf((fi.z - G.lo[2]) * G.inv_cell), 0), G.dims[2] - 1);
-            for (int dz = -1; dz <= 1; ++dz) {
-                int z = cz + dz;
-                if (z < 0 || z >= G.dims[2]) continue;
-                for (int dy = -1; dy <= 1; ++dy) {
-                    int y = cy + dy;
-                    if (y < 0 || y >= G.dims[1]) continue;
-                    int row = G.base + (z * G.dims[1] + y) * G.dims[0];
-                    int x0 = max(cx - 1, 0), x1 = min(cx + 1, G.dims[0] - 1);
-                    int beg = A.cstart[row + x0], end = A.cstart[row + x1 + 1];
-                    for (int b0 = beg; b0 < end; b0 += 32) {
-                        int k = b0 + lane;
-                        bool ok = false;
-                        int j = -1;
-                        if (k < end) {
-                            float4 fj = A.sf4[k];
-                            j = A.sidx[k];
-                            float dx = fj.x - fi.x, dy2 = fj.y - fi.y, dz2 = fj.z - fi.z;
-                            float rr = fi.w + fj.w + G.margin;
-                            ok = (j != i) && (dx * dx + dy2 * dy2 + dz2 * dz2 < rr * rr);
+        // ---------------- neighbour candidates: balls that may overlap B_i (from this atom's
+        // Verlet list when every atom stayed within half the skin of its reference position)
+        const bool reuse = A.reuse != nullptr && *A.reuse != 0;
+        if (reuse) {
+            nc = A.nbn[i];
+            for (int k = lane; k < min(nc, KMAX); k += 32) S->pg[NG + k] = A.nbl[(size_t)i * NBL_CAP + k];
+        } else {
+            {
+                int cx = min(max((int)floorf((fi.x - G.lo[0]) * G.inv_cell), 0), G.dims[0] - 1);
+                int cy = min(max((int)floorf((fi.y - G.lo[1]) * G.inv_cell), 0), G.dims[1] - 1);
+                int cz = min(max((int)floorf((fi.z - G.lo[2]) * G.inv_cell), 0), G.dims[2] - 1);
+                for (int dz = -1; dz <= 1; ++dz) {
+                    int z = cz + dz;
+                    if (z < 0 || z >= G.dims[2]) continue;
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        int y = cy + dy;
+                        if (y < 0 || y >= G.dims[1]) continue;
+                        int row = G.base + (z * G.dims[1] + y) * G.dims[0];
+                        int x0 = max(cx - 1, 0), x1 = min(cx + 1, G.dims[0] - 1);
+                        int beg = A.cstart[row + x0], end = A.cstart[row + x1 + 1];
+                        for (int b0 = beg; b0 < end; b0 += 32) {
+                            int k = b0 + lane;
+                            bool ok = false;
+                            int j = -1;
+                            if (k < end) {
+                                float4 fj = A.sf4[k];
+                                j = A.sidx[k];
+                                float dx = fj.x - fi.x, dy2 = fj.y - fi.y, dz2 = fj.z - fi.z;
+                                float rr = fi.w + fj.w + G.margin;
+                                ok = (j != i) && (dx * dx + dy2 * dy2 + dz2 * dz2 < rr * rr);
+                            }
+                            unsigned bal = __ballot_sync(FULL, ok);
+                            int pos = nc + __popc(bal & lanemask_lt());
+                            if (ok && pos < KMAX) S->pg[NG + pos] = j;
+                            nc += __popc(bal);
                         }
-                        unsigned bal = __ballot_sync(FULL, ok);
-                        int pos = nc + __popc(bal & lanemask_lt());
-                        if (ok && pos < KMAX) S->pg[NG + pos] = j;
-                        nc += __popc(bal);
                     }
+                }
+            }
+            if (A.nbl) {
+                // store the list and the reference position for the next calls (a deferred
+                // atom's list is stored by the large-capacity pass, which gathers all of it)
+                __syncwarp();
+                if (nc <= KMAX) {
+                    for (int k = lane; k < nc; k += 32) A.nbl[(size_t)i * NBL_CAP + k] = S->pg[NG + k];
+                    if (lane == 0) A.nbn[i] = nc;
+                } else if (!can_defer && lane == 0) {
+                    atomicOr(A.lists_bad, 1);
+                }
+                if (lane == 0) {
+                    for (int k = 0; k < 3; ++k) A.ref_xyz[3 * i + k] = A.xyz[3 * i + k];
+                    A.ref_rad[i] = A.radii_in[i];
                 }
             }
         }

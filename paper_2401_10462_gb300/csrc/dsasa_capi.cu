@@ -42,6 +42,14 @@ struct dsasa_ctx {
     long long* offsets = nullptr;
     int* defer = nullptr;       // atoms the fast kernel pass defers to the large pass
     unsigned char* cells = nullptr;   // per-atom cell records between the cell and terms kernels
+    // Verlet lists (skin > 0): candidates per atom, reference coordinates / radii, state
+    int* nbl = nullptr;
+    int* nbn = nullptr;
+    double* ref_xyz = nullptr;
+    double* ref_rad = nullptr;
+    int* vstate = nullptr;        // [0] max displacement^2 (float bits), [1] radii changed, [2] reuse, [3] overflow
+    int64_t lists_n = 0;          // the lists hold this many atoms of the last single-molecule call
+    double lists_probe = -1.0;
     int* status = nullptr;      // [0] status bits, [1] total cells, [2] deferred count
     // optional per-kernel timing: events of up to kTimingRing calls since the last read
     bool timing = false;
@@ -87,6 +95,8 @@ void free_scratch(dsasa_ctx* c) {
     dfree(c->R); dfree(c->Rhl); dfree(c->f4); dfree(c->molid); dfree(c->rank); dfree(c->cell); dfree(c->sidx); dfree(c->sf4);
     dfree(c->bbox); dfree(c->grids); dfree(c->counts); dfree(c->cstart); dfree(c->blocksums); dfree(c->offsets);
     dfree(c->defer); dfree(c->cells);
+    dfree(c->nbl); dfree(c->nbn); dfree(c->ref_xyz); dfree(c->ref_rad); dfree(c->vstate);
+    c->lists_n = 0;
     c->cap_atoms = c->cap_mol = c->cap_cells = 0;
 }
 void free_host_staging(dsasa_ctx* c) {
@@ -119,6 +129,11 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
     ALLOC(R, na) ALLOC(Rhl, na) ALLOC(f4, na) ALLOC(molid, na) ALLOC(rank, na) ALLOC(cell, na) ALLOC(sidx, na) ALLOC(sf4, na)
     ALLOC(bbox, 8 * nm) ALLOC(grids, nm) ALLOC(counts, nc + 1) ALLOC(cstart, nc + 1) ALLOC(blocksums, nbs)
     ALLOC(offsets, nm + 1) ALLOC(defer, na) ALLOC(cells, na * (int64_t)cell_record_bytes())
+    if (c->cfg.skin > 0.0) {
+        ALLOC(nbl, na * NBL_CAP) ALLOC(nbn, na) ALLOC(ref_xyz, 3 * na) ALLOC(ref_rad, na) ALLOC(vstate, 4)
+        e = cudaMemsetAsync(c->vstate, 0, 4 * sizeof(int), c->stream);
+        if (e != cudaSuccess) { free_scratch(c); return cuda_fail(c, e, "memset"); }
+    }
 #undef ALLOC
     c->cap_atoms = na;
     c->cap_mol = nm;
@@ -128,8 +143,9 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
 
 // the cell list of the inputs in the context's scratch (enqueued on its stream)
 cudaError_t build_cells(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n, int n_mol,
-                        const long long* offsets_dev) {
+                        const long long* offsets_dev, const int* skip = nullptr) {
     BuildArgs b{};
+    b.skip = skip;
     b.xyz = coords;
     b.radii = radii;
     b.probe = probe;
@@ -151,7 +167,15 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     if (st != DSASA_OK) return st;
     cudaEvent_t* ev = (c->timing && c->n_timed < kTimingRing) ? c->ev[c->n_timed++] : nullptr;
     if (ev) cudaEventRecord(ev[0], c->stream);
-    cudaError_t e = build_cells(c, coords, radii, probe, n, n_mol, offsets_dev);
+    // Verlet lists: reused on the device when every atom stayed within half the skin
+    const bool lists = c->nbl != nullptr && n_mol == 1;
+    if (lists) {
+        const int valid = c->lists_n == n && c->lists_probe == probe;
+        cudaError_t ev_e = launch_verlet_check(coords, radii, c->ref_xyz, c->ref_rad, (int)n, valid, c->cfg.skin,
+                                               c->vstate, c->stream);
+        if (ev_e != cudaSuccess) return cuda_fail(c, ev_e, "Verlet check launch");
+    }
+    cudaError_t e = build_cells(c, coords, radii, probe, n, n_mol, offsets_dev, lists ? c->vstate + 2 : nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "cell-list launch");
     if (ev) cudaEventRecord(ev[1], c->stream);
     AtomArgs a{};
@@ -178,9 +202,21 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     a.defer_count = c->status + 2;
     a.cells = c->cells;
     a.ev = ev ? ev + 2 : nullptr;
+    if (lists) {
+        a.nbl = c->nbl;
+        a.nbn = c->nbn;
+        a.reuse = c->vstate + 2;
+        a.lists_bad = c->vstate + 3;
+        a.ref_xyz = c->ref_xyz;
+        a.ref_rad = c->ref_rad;
+        a.radii_in = radii;
+    }
     e = c->cfg.precision == DSASA_FP64 ? launch_atoms_f64(a, grad != nullptr, c->stream)
                                        : launch_atoms_f32(a, grad != nullptr, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "atom kernel launch");
+    // the lists now describe this call's molecule (or none: another layout overwrote the cells)
+    c->lists_n = lists ? n : 0;
+    c->lists_probe = probe;
     return DSASA_OK;
 }
 
@@ -286,6 +322,7 @@ dsasa_status dsasa_compute_sr(dsasa_ctx* c, const double* coords, const double* 
     if (st != DSASA_OK) return st;
     cudaError_t e = build_cells(c, coords, radii, probe, n, 1, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "cell-list launch");
+    c->lists_n = 0;   // the cell list now belongs to this call
     SRArgs a{};
     a.xyz = coords;
     a.R = c->R;
@@ -304,6 +341,19 @@ dsasa_status dsasa_compute_sr(dsasa_ctx* c, const double* coords, const double* 
     if (c->sr_tests) cudaMemsetAsync(c->sr_tests, 0, sizeof(unsigned long long), c->stream);
     e = launch_sr(a, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "Shrake-Rupley launch");
+    return DSASA_OK;
+}
+
+dsasa_status dsasa_lists_reused(dsasa_ctx* c, int* reused) {
+    if (!c || !reused) return DSASA_ERR_ARG;
+    *reused = 0;
+    if (!c->vstate) return DSASA_OK;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    int h[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, c->vstate, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "list state read");
+    *reused = h[2];
     return DSASA_OK;
 }
 

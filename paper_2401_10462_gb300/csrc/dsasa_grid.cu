@@ -32,6 +32,7 @@ __global__ void k_bbox_init(unsigned* bbox, int n_mol) {
 }
 
 __global__ void k_prep(BuildArgs a) {
+    if (a.skip && *a.skip) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = i < a.n;
     const unsigned mask = __ballot_sync(0xffffffffu, act);
@@ -113,7 +114,7 @@ __device__ MolGrid make_grid(const unsigned* bb, long long nm, double skin) {
     }
     for (int k = 0; k < 3; ++k) { g.lo[k] = lo[k]; g.dims[k] = dims[k]; }
     g.inv_cell = 1.0f / cell;
-    g.margin = margin + 0.5f * (float)skin;
+    g.margin = margin + (float)skin;   // candidates within R_i + R_j + skin (Verlet lists)
     g.rmax = rmax;
     g.base = dims[0] * dims[1] * dims[2];
     return g;
@@ -121,6 +122,7 @@ __device__ MolGrid make_grid(const unsigned* bb, long long nm, double skin) {
 
 // per molecule: cell size and dimensions (cell count stored in base for the scan below)
 __global__ void k_grid_local(BuildArgs a) {
+    if (a.skip && *a.skip) return;
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= a.n_mol) return;
     long long nm = a.offsets ? (a.offsets[m + 1] - a.offsets[m]) : a.n;
@@ -129,6 +131,7 @@ __global__ void k_grid_local(BuildArgs a) {
 
 // exclusive scan of the per-molecule cell counts (one block)
 __global__ void k_grid_scan(BuildArgs a) {
+    if (a.skip && *a.skip) return;
     __shared__ int carry;
     __shared__ int ws[32];
     if (threadIdx.x == 0) carry = 0;
@@ -173,6 +176,7 @@ __device__ __forceinline__ int cell_of(const MolGrid& g, float4 f) {
 }
 
 __global__ void k_count(BuildArgs a) {
+    if (a.skip && *a.skip) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const MolGrid g = a.grids[a.molid[i]];
@@ -246,6 +250,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(const int* in, int len, co
 }
 
 __global__ void k_scatter(BuildArgs a) {
+    if (a.skip && *a.skip) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     int pos = a.cstart[a.cell[i]] + a.rank[i];
@@ -257,6 +262,7 @@ __global__ void k_scatter(BuildArgs a) {
 // (the multi-kernel path's launch overheads dominate at that size).  Same grid, same cells.
 constexpr int kSmallAtoms = 16384, kSmallT = 1024, kSmallCells = 8192;
 __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
+    if (a.skip && *a.skip) return;
     __shared__ unsigned bb[8];
     __shared__ MolGrid g;
     __shared__ int ws[kSmallT / 32];
@@ -378,6 +384,47 @@ cudaError_t launch_build_multi(const BuildArgs& a, cudaStream_t s) {
 }  // namespace
 
 size_t scan_scratch_ints(int max_cells) { return (size_t)(max_cells + 1 + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+namespace {
+
+// Verlet skin test (see dsasa_kernels.cuh)
+__global__ void k_verlet_check(const double* xyz, const double* radii, const double* ref_xyz, const double* ref_rad,
+                               int n, int* vstate) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float d2 = 0.f;
+    int changed = 0;
+    if (i < n) {
+        double dx = xyz[3 * i] - ref_xyz[3 * i], dy = xyz[3 * i + 1] - ref_xyz[3 * i + 1], dz = xyz[3 * i + 2] - ref_xyz[3 * i + 2];
+        double dd = dx * dx + dy * dy + dz * dz;
+        d2 = (float)dd * (1.f + 1e-6f);   // rounded up: the test stays conservative
+        if (!(dd == dd)) d2 = INFINITY;
+        changed = radii[i] != ref_rad[i];
+    }
+    const unsigned d2max = __reduce_max_sync(0xffffffffu, __float_as_uint(d2));   // d2 >= 0: bits order as values
+    changed = __reduce_or_sync(0xffffffffu, changed);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax((unsigned*)&vstate[0], d2max);
+        if (changed) atomicOr(&vstate[1], 1);
+    }
+}
+__global__ void k_verlet_decide(int* vstate, int valid, float lim2) {
+    const float d2 = __uint_as_float((unsigned)vstate[0]);
+    const int reuse = valid && vstate[1] == 0 && vstate[3] == 0 && d2 <= lim2;
+    vstate[2] = reuse;
+    if (!reuse) vstate[3] = 0;   // the lists are rebuilt by this call
+}
+
+}  // namespace
+
+cudaError_t launch_verlet_check(const double* xyz, const double* radii, const double* ref_xyz, const double* ref_rad,
+                                int n, int valid, double skin, int* vstate, cudaStream_t s) {
+    cudaMemsetAsync(vstate, 0, 2 * sizeof(int), s);
+    if (valid && n > 0) k_verlet_check<<<(n + 255) / 256, 256, 0, s>>>(xyz, radii, ref_xyz, ref_rad, n, vstate);
+    // (skin / 2)^2, rounded down in float
+    float lim2 = (float)(0.25 * skin * skin) * (1.f - 1e-6f);
+    k_verlet_decide<<<1, 1, 0, s>>>(vstate, valid, lim2);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;

@@ -36,6 +36,7 @@ struct BuildArgs {
     int n_mol;
     const long long* offsets;   // device, n_mol + 1 (NULL: one molecule)
     double skin;
+    const int* skip;   // non-NULL and *skip != 0: the previous cell list is reused (nothing to do)
     int max_cells;
     // outputs / scratch
     double* R;         // n
@@ -87,7 +88,20 @@ struct AtomArgs {
     // optional timing: events recorded on the stream after the cell, classification, terms
     // and large-capacity kernels (NULL = none)
     cudaEvent_t* ev;
+    // Verlet neighbour lists (single molecule, skin > 0; NULL = none): candidates of atom i
+    // at nbl[i * NBL_CAP .. + nbn[i]).  *reuse != 0: take the candidates from the lists (the
+    // cell list was not rebuilt); else gather them from the cell list and store them with
+    // the reference coordinates and radii.  *lists_bad is set when a list cannot hold its
+    // atom's candidates (the next call rebuilds).
+    int* nbl;
+    int* nbn;
+    const int* reuse;
+    int* lists_bad;
+    double* ref_xyz;
+    double* ref_rad;
+    const double* radii_in;
 };
+constexpr int NBL_CAP = 122;   // list capacity per atom (the large-capacity pass's)
 
 // Shrake-Rupley numerical SASA (cross-check): m unit vectors pts[3m] (device)
 struct SRArgs {
@@ -108,6 +122,10 @@ struct SRArgs {
 };
 
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t s);
+// Verlet skin test: vstate[2] = reuse the lists (valid, every atom within skin/2 of its
+// reference position, radii unchanged, no list overflow); vstate[0..1] scratch, [3] overflow
+cudaError_t launch_verlet_check(const double* xyz, const double* radii, const double* ref_xyz, const double* ref_rad,
+                                int n, int valid, double skin, int* vstate, cudaStream_t s);
 cudaError_t launch_sr(const SRArgs& a, cudaStream_t s);
 cudaError_t launch_atoms_f32(const AtomArgs& a, bool grad, cudaStream_t s);
 cudaError_t launch_atoms_f64(const AtomArgs& a, bool grad, cudaStream_t s);
