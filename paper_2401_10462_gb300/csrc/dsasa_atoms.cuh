@@ -380,8 +380,24 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         // Verlet list when every atom stayed within half the skin of its reference position)
         const bool reuse = A.reuse != nullptr && *A.reuse != 0;
         if (reuse) {
-            nc = A.nbn[i];
-            for (int k = lane; k < min(nc, KMAX); k += 32) S->pg[NG + k] = A.nbl[(size_t)i * NBL_CAP + k];
+            // the list holds every atom within R_i + R_j + skin at the last rebuild; keep the
+            // ones whose balls overlap B_i now (float64, with a relative slack of 1e-9)
+            const int nl = A.nbn[i];
+            for (int b0 = 0; b0 < nl; b0 += 32) {
+                const int k = b0 + lane;
+                bool ok = false;
+                int j = -1;
+                if (k < nl) {
+                    j = A.nbl[(size_t)i * NBL_CAP + k];
+                    const double dx = A.xyz[3 * j] - c.pi[0], dy = A.xyz[3 * j + 1] - c.pi[1], dz = A.xyz[3 * j + 2] - c.pi[2];
+                    const double rr = c.Ri + A.R[j];
+                    ok = dx * dx + dy * dy + dz * dz < rr * rr * (1.0 + 1e-9);
+                }
+                unsigned bal = __ballot_sync(FULL, ok);
+                int pos = nc + __popc(bal & lanemask_lt());
+                if (ok && pos < KMAX) S->pg[NG + pos] = j;
+                nc += __popc(bal);
+            }
         } else {
             {
                 int cx = min(max((int)floorf((fi.x - G.lo[0]) * G.inv_cell), 0), G.dims[0] - 1);
