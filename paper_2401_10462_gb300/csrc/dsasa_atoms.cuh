@@ -53,7 +53,7 @@ enum { CELL_OK = 0, CELL_DONE = 1 };   // record flag: CELL_DONE = outputs alrea
 template <class R, int NE, int NT> struct Smem {
     using Real = R;
     static constexpr int kNE = NE, kNT = NT;
-    R pq[NE][4];          // plane q.x, q.y, q.z, b (relative to p_i)
+    alignas(16) R pq[NE][4];   // plane q.x, q.y, q.z, b (relative to p_i)
     R pB[NE];             // magnitude proxy of b for the filters
     int pg[NE];           // global atom index (>= 0) or -1 - ghost id
     uint8_t start[NE];    // a vertex slot on the face of this plane
@@ -77,7 +77,7 @@ template <class R, int NE, int NT> struct Smem {
 // The cell of one atom between the two kernels (first NG + nc plane entries, first hw
 // vertex slots used).
 template <class R, int NE, int NT> struct CellRec {
-    R pq[NE][4];
+    alignas(16) R pq[NE][4];
     R pB[NE];
     int pg[NE];
     uchar4 tv[NT];
@@ -89,6 +89,16 @@ template <class R, int NE, int NT> struct CellRec {
     int iK, icl;
     int nc, hw, flag, pad;
 };
+
+// one plane row (4 values of R) between the shared table and a cell record, 16-byte moves
+template <class R> __device__ __forceinline__ void copy_row(R* dst, const R* src) {
+    if constexpr (sizeof(R) == 4) {
+        *(float4*)dst = *(const float4*)src;
+    } else {
+        ((double2*)dst)[0] = ((const double2*)src)[0];
+        ((double2*)dst)[1] = ((const double2*)src)[1];
+    }
+}
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -477,7 +487,9 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             if (e < NG) S->pg[e] = g;
             for (int k = 0; k < 3; ++k) S->pq[e][k] = (R)q[k];
             S->pq[e][3] = (R)b;
-            if (sizeof(R) == 4) S->pB[e] = (R)(fabs((double)(float)b) * (1.0 + 1.2e-7) + babs * 1.4901161193847656e-08);
+            // magnitude proxy of b in float: |b_f| (1 + 2^-22) + 2^-26 babs, rounded up (the float
+            // evaluation loses at most 2 ulp, covered by the larger factors)
+            if (sizeof(R) == 4) S->pB[e] = (R)(fabsf((float)b) * 1.0000003f + (float)babs * 1.5e-8f);
             else S->pB[e] = (R)(ex ? fabs(b) : 8.0 * babs);
             S->start[e] = NONE;
             if (e >= NG) {
@@ -773,7 +785,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             // hand the cell to the terms kernel
             const int np = NG + nc, hw = S->hw;
             for (int e = lane; e < np; e += 32) {
-                for (int k = 0; k < 4; ++k) rec->pq[e][k] = S->pq[e][k];
+                copy_row(rec->pq[e], S->pq[e]);
                 rec->pB[e] = S->pB[e];
                 rec->pg[e] = S->pg[e];
                 rec->start[e] = S->start[e];
@@ -797,7 +809,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             const int np = NG + nc, hw = rec->hw;
             nrounds = (hw + 31) >> 5;
             for (int e = lane; e < np; e += 32) {
-                for (int k = 0; k < 4; ++k) S->pq[e][k] = rec->pq[e][k];
+                copy_row(S->pq[e], rec->pq[e]);
                 S->pB[e] = rec->pB[e];
                 S->pg[e] = rec->pg[e];
                 S->start[e] = rec->start[e];
