@@ -1,6 +1,6 @@
-// The per-atom kernel: one warp builds atom i's restricted Laguerre cell, classifies the
+// The per-atom kernels: a warp builds atom i's restricted Laguerre cell, classifies the
 // simplices of the dual complex C that contain i, and evaluates A_i and the gradient entry
-// of atom i.  Nothing goes through global memory between these steps.
+// of atom i (and, on request, the atom's molecular-volume share).
 //
 //   Step 1 (paper): the weighted Delaunay tetrahedra around i are the vertices of the power
 //     cell L_i.  The warp starts from a cube (6 ghost planes at distance h > R_i) and clips
@@ -18,8 +18,12 @@
 //   Step 3: A_i by Eq. (sainexclu); the gradient entry of atom i gathers, over the simplices
 //     of C containing i, the derivative of every atom's terms (Eq. inexclu) - no atomics.
 //
-// One warp per atom; the cell lives in shared memory (plane table, triangle table) and in
-// registers (each lane caches the homogeneous coordinates of up to 4 cell vertices).
+// One warp per atom (two per block); the cell lives in shared memory (plane table, triangle
+// table) and in registers (each lane caches the homogeneous coordinates of up to NT / 32
+// cell vertices).  The fast path runs the steps as separate kernels that hand the cell over
+// through a per-atom record in HBM (PH_CELL: Step 1; PH_CLASS: Step 2; PH_TERMS: Step 3;
+// PH_VOL: the volume), so that each kernel's code fits the instruction cache; the fused form
+// (PH_ALL) serves the large-capacity pass and the no-allocation entry point.
 #pragma once
 #include "dsasa_kernels.cuh"
 #include "dsasa_math.cuh"
