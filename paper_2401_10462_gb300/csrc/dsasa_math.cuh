@@ -393,8 +393,6 @@ DS_HD double cap64(double d, double R1, double R2) {
 }
 // distance from the centre of sphere 1 to the plane of the circle where spheres 1, 2 meet
 template <class T> DS_HD T t_dist(T d, T R1, T R2) { return (d * d + R1 * R1 - R2 * R2) / ((T)2 * d); }
-// cap of sphere 1 inside ball 2 (Eq. edge): 2 pi R1 h1, h1 = R1 - t1
-template <class T> DS_HD T cap_area(T d, T R1, T R2) { return (T)2 * pi_t<T>() * R1 * (R1 - t_dist(d, R1, R2)); }
 
 // one of the two points common to the three sphere surfaces; false if none
 template <class T> DS_HD bool triple_point(P3<T> p1, P3<T> p2, P3<T> p3, T R1, T R2, T R3, P3<T>& x) {
