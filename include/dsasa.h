@@ -172,6 +172,11 @@ dsasa_status dsasa_deferred_count(dsasa_ctx* ctx, int64_t* deferred);
 dsasa_status dsasa_set_timing(dsasa_ctx* ctx, int enable);
 dsasa_status dsasa_kernel_times(dsasa_ctx* ctx, double* ms_out, int64_t* calls_out);
 
+/* Number of CUDA kernels this library has launched since it was loaded, over all contexts and
+ * the no-allocation entry point (host-side count of launch statements; cudaMemsetAsync is not
+ * counted).  Diagnostics, no paper counterpart; thread-safe. */
+int64_t dsasa_kernel_launches(void);
+
 /* Diagnostic export of the dual complex C as seen by each atom's local cell.  For every atom
  * i and every simplex of C that contains i, one record of 5 int32 is written to `records`
  * (device, capacity `max_records`): {i, v0, v1, v2, v3} with the simplex's atom indices in

@@ -22,8 +22,10 @@
 // table) and in registers (each lane caches the homogeneous coordinates of up to NT / 32
 // cell vertices).  The fast path runs the steps as separate kernels that hand the cell over
 // through a per-atom record in HBM (PH_CELL: Step 1; PH_CLASS: Step 2; PH_TERMS: Step 3;
-// PH_VOL: the volume), so that each kernel's code fits the instruction cache; the fused form
-// (PH_ALL) serves the large-capacity pass and the no-allocation entry point.
+// PH_VOL: the volume), so that each kernel's code fits the instruction cache.  When all atoms
+// fit in one wave, Steps 1 and 2 run as one kernel (PH_CC), so that classifications overlap
+// the slowest cells.  The fused form (PH_ALL) serves the large-capacity pass and the
+// no-allocation entry point.
 #pragma once
 #include "dsasa_kernels.cuh"
 #include "dsasa_math.cuh"
@@ -47,7 +49,7 @@ constexpr int MINB = 32, MINB_CELL = 18, MINB_CLASS = 18, MINB_TERMS = 18;
 // through a global record per atom: the cell construction (gather, sort, clipping), the
 // classification (Steps 2a-2c: which simplices of the cell are in C), and the area terms and
 // gradient.  Each kernel's code then fits the instruction cache.
-enum { PH_ALL = 0, PH_CELL = 1, PH_CLASS = 2, PH_TERMS = 3, PH_VOL = 4 };
+enum { PH_ALL = 0, PH_CELL = 1, PH_CLASS = 2, PH_TERMS = 3, PH_VOL = 4, PH_CC = 5 };
 enum { CELL_OK = 0, CELL_DONE = 1 };   // record flag: CELL_DONE = outputs already written
 
 // Per-warp cell storage.  NE plane entries (0..5 ghosts, then the candidates in sorted
@@ -324,10 +326,10 @@ template <class SM, class R = typename SM::Real> __device__ __forceinline__ P3<R
 
 // ------------------------------------------------------------------ the kernel
 __host__ __device__ constexpr int minb(int ph) {
-    return ph == PH_CELL ? MINB_CELL : (ph == PH_CLASS ? MINB_CLASS : ((ph == PH_TERMS || ph == PH_VOL) ? MINB_TERMS : MINB));
+    return (ph == PH_CELL || ph == PH_CC) ? MINB_CELL : (ph == PH_CLASS ? MINB_CLASS : ((ph == PH_TERMS || ph == PH_VOL) ? MINB_TERMS : MINB));
 }
 __host__ __device__ constexpr int warps_of(int ph) {
-    return ph == PH_CELL ? WARPS_CELL : (ph == PH_CLASS ? WARPS_CLASS : ((ph == PH_TERMS || ph == PH_VOL) ? WARPS_TERMS : WARPS));
+    return (ph == PH_CELL || ph == PH_CC) ? WARPS_CELL : (ph == PH_CLASS ? WARPS_CLASS : ((ph == PH_TERMS || ph == PH_VOL) ? WARPS_TERMS : WARPS));
 }
 template <class R, bool GRAD, int NE, int NT, int PH>
 __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs A) {
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         const FA<R> wi = {Rr * Rr, Rr * Rr};
         CellRec<R, NE, NT>* rec = (CellRec<R, NE, NT>*)A.cells + s;
         auto done = [&]() {   // the outputs of this atom are written: tell the terms kernel
-            if ((PH == PH_CELL || PH == PH_CLASS) && lane == 0) rec->flag = CELL_DONE;
+            if ((PH == PH_CELL || PH == PH_CLASS || PH == PH_CC) && lane == 0) rec->flag = CELL_DONE;
         };
 
         int nc = 0;
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             }
         };
 
-        if constexpr (PH == PH_ALL || PH == PH_CELL) {
+        if constexpr (PH == PH_ALL || PH == PH_CELL || PH == PH_CC) {
         // ---------------- neighbour candidates: balls that may overlap B_i (from this atom's
         // Verlet list when every atom stayed within half the skin of its reference position)
         const bool reuse = A.reuse != nullptr && *A.reuse != 0;
@@ -785,7 +787,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             __syncwarp();
             continue;
         }
-        if constexpr (PH == PH_CELL) {
+        if constexpr (PH == PH_CELL || PH == PH_CC) {
             // hand the cell to the terms kernel
             const int np = NG + nc, hw = S->hw;
             for (int e = lane; e < np; e += 32) {
@@ -804,7 +806,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 rec->flag = CELL_OK;
             }
             __syncwarp();
-            continue;
+            if constexpr (PH == PH_CELL) continue;
         }
         } else {
             // ---------------- the cell built by the cell kernel
@@ -1092,7 +1094,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         }
 
         }
-        if constexpr (PH == PH_CLASS) {
+        if constexpr (PH == PH_CLASS || PH == PH_CC) {
             __syncwarp();
             if (S->bad) {
                 if (lane == 0) {
@@ -1100,7 +1102,6 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                     A.areas[i] = __longlong_as_double(0x7ff8000000000000ll);
                     if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
                     if (A.vol) A.vol[i] = __longlong_as_double(0x7ff8000000000000ll);
-                if (A.vol) A.vol[i] = __longlong_as_double(0x7ff8000000000000ll);
                 }
                 done();
                 __syncwarp();
@@ -1311,6 +1312,22 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
 }  // namespace
 
 #ifndef DSASA_ATOMS_NO_LAUNCH
+// Whether every atom's warp of the cell kernel is resident at once (one wave).  Then the fused
+// cell + classification kernel runs an atom's classification while other atoms are still
+// clipping (the slowest cells set the end of the wave); with more atoms the split kernels keep
+// each kernel's instruction stream in the cache, which is worth more.
+template <class R> bool cells_in_one_wave(int n) {
+    static int cap = -1;
+    if (cap < 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_atoms<R, false, 64, 64, PH_CC>, WARPS_CELL * 32, 0);
+        cap = sms * per * WARPS_CELL;
+    }
+    return n <= cap;
+}
+
 // Fast pass (64 planes, 64 vertex slots) over all atoms: with a cell store, the cell,
 // classification and terms kernels, else the fused kernel.  The atoms it defers get the fused 128 / 128
 // pass, whose grid reads the deferred count from device memory (no host sync).
@@ -1337,17 +1354,27 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     };
     if (a.cells) {
         auto nb = [&](int w) { return (a.n + w - 1) / w; };
-        k_atoms<R, false, 64, 64, PH_CELL><<<nb(WARPS_CELL), WARPS_CELL * 32, 0, s>>>(fast);
-        mark(0);
-        k_atoms<R, false, 64, 64, PH_CLASS><<<nb(WARPS_CLASS), WARPS_CLASS * 32, 0, s>>>(fast);
-        mark(1);
+        if (cells_in_one_wave<R>(a.n)) {
+            k_atoms<R, false, 64, 64, PH_CC><<<nb(WARPS_CELL), WARPS_CELL * 32, 0, s>>>(fast);
+            note_launches(1);
+            mark(0);
+            mark(1);
+        } else {
+            k_atoms<R, false, 64, 64, PH_CELL><<<nb(WARPS_CELL), WARPS_CELL * 32, 0, s>>>(fast);
+            mark(0);
+            k_atoms<R, false, 64, 64, PH_CLASS><<<nb(WARPS_CLASS), WARPS_CLASS * 32, 0, s>>>(fast);
+            note_launches(2);
+            mark(1);
+        }
         if (g) k_atoms<R, true, 64, 64, PH_TERMS><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
         else k_atoms<R, false, 64, 64, PH_TERMS><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
         if (a.vol) k_atoms<R, false, 64, 64, PH_VOL><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
+        note_launches(a.vol ? 2 : 1);
         mark(2);
     } else {
         if (g) k_atoms<R, true, 64, 64, PH_ALL><<<blocks, WARPS * 32, 0, s>>>(fast);
         else k_atoms<R, false, 64, 64, PH_ALL><<<blocks, WARPS * 32, 0, s>>>(fast);
+        note_launches(1);
         mark(0);
         mark(1);
         mark(2);
@@ -1355,6 +1382,7 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     if (a.defer_list) {
         if (g) k_atoms<R, true, 128, 128, PH_ALL><<<big_blocks, WARPS * 32, 0, s>>>(big);
         else k_atoms<R, false, 128, 128, PH_ALL><<<big_blocks, WARPS * 32, 0, s>>>(big);
+        note_launches(1);
     }
     mark(3);
     return cudaGetLastError();

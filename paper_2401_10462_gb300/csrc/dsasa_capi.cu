@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,6 +17,11 @@
 using namespace dsasa;
 
 constexpr int kTimingRing = 256;
+
+namespace {
+std::atomic<long long> g_launches{0};   // kernels launched by this library (all contexts)
+}
+void dsasa::note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 struct dsasa_ctx {
     int device = 0;
@@ -482,6 +488,8 @@ dsasa_status dsasa_export_complex(dsasa_ctx* c, const double* coords, const doub
 }
 
 const char* dsasa_last_error(const dsasa_ctx* c) { return c ? c->err : "null context"; }
+
+int64_t dsasa_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 dsasa_status dsasa_set_timing(dsasa_ctx* c, int enable) {
     if (!c) return DSASA_ERR_ARG;

@@ -378,6 +378,7 @@ cudaError_t launch_build_multi(const BuildArgs& a, cudaStream_t s) {
     k_scan_top<<<1, SCAN_T, 0, s>>>(a.blocksums, nt);
     k_scan_down<<<nt, SCAN_T, 0, s>>>(a.counts, len, a.blocksums, a.cstart);
     k_scatter<<<nb, T, 0, s>>>(a);
+    note_launches(9);
     return cudaGetLastError();
 }
 
@@ -419,10 +420,14 @@ __global__ void k_verlet_decide(int* vstate, int valid, float lim2) {
 cudaError_t launch_verlet_check(const double* xyz, const double* radii, const double* ref_xyz, const double* ref_rad,
                                 int n, int valid, double skin, int* vstate, cudaStream_t s) {
     cudaMemsetAsync(vstate, 0, 2 * sizeof(int), s);
-    if (valid && n > 0) k_verlet_check<<<(n + 255) / 256, 256, 0, s>>>(xyz, radii, ref_xyz, ref_rad, n, vstate);
+    if (valid && n > 0) {
+        k_verlet_check<<<(n + 255) / 256, 256, 0, s>>>(xyz, radii, ref_xyz, ref_rad, n, vstate);
+        note_launches(1);
+    }
     // (skin / 2)^2, rounded down in float
     float lim2 = (float)(0.25 * skin * skin) * (1.f - 1e-6f);
     k_verlet_decide<<<1, 1, 0, s>>>(vstate, valid, lim2);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -430,6 +435,7 @@ cudaError_t launch_build(const BuildArgs& a, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     if (a.n_mol == 1 && a.n <= kSmallAtoms) {
         k_build_small<<<1, kSmallT, 0, s>>>(a);
+        note_launches(1);
         return cudaGetLastError();
     }
     return launch_build_multi(a, s);

@@ -5,6 +5,9 @@
 
 namespace dsasa {
 
+// host: adds k to the library-wide count of kernel launches (dsasa_kernel_launches)
+void note_launches(int k);
+
 // device status bits (ORed by kernels, read by dsasa_status_sync)
 enum : int {
     ST_CAND_OVF = 1,      // more overlapping neighbours than one warp's candidate table holds

@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_shrake_rupley(SRArgs A) {
 cudaError_t launch_sr(const SRArgs& a, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     k_shrake_rupley<<<(a.n + SR_WARPS - 1) / SR_WARPS, SR_WARPS * 32, 0, s>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -181,6 +181,51 @@ def test_batch_equals_separate(api, torch_cuda, gen):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_one_wave_and_split_kernels_agree(api, torch_cuda, orc, gen, precision):
+    """A molecule alone (few atoms: the cell and classification steps run as one kernel) and
+    the same molecule inside a batch of more atoms than one wave of the cell kernel holds
+    (separate cell and classification kernels) give bit-identical results."""
+    torch = torch_cuda
+    small, big = gen.globule(304, 11), gen.globule(7000, 12)
+    xyz = np.concatenate([small.coords, big.coords])
+    r = np.concatenate([small.radii, big.radii])
+    off = np.array([0, small.n, small.n + big.n])
+    ctx = api.Context(precision=precision)
+    a = torch.empty(len(r), dtype=torch.float64, device="cuda")
+    g = torch.empty((len(r), 3), dtype=torch.float64, device="cuda")
+    k0 = api.kernel_launches()
+    ctx.compute_batch(off, _dev(torch, xyz), _dev(torch, r), a, g)
+    ctx.status_sync()
+    # multi-molecule cell-list build (9), cell, classification, terms, large-capacity pass
+    assert api.kernel_launches() - k0 == 9 + 4
+    a1, g1 = gpu_sasa(api, torch, small.coords, small.radii, precision)
+    assert np.array_equal(a.cpu().numpy()[:small.n], a1)
+    assert np.array_equal(g.cpu().numpy()[:small.n], g1)
+    ra, _, rg = orc.sasa(small.coords, small.radii)
+    check_areas(a1, ra)
+    check_grad(g1, rg)
+
+
+def test_kernel_launch_count(api, torch_cuda, gen):
+    """The library's launch counter: one small molecule takes the one-block cell-list build,
+    the fused cell + classification kernel, the terms kernel and the (empty) large pass."""
+    torch = torch_cuda
+    m = gen.globule(304, 2)
+    ctx = api.Context()
+    x, r = _dev(torch, m.coords), _dev(torch, m.radii)
+    a = torch.empty(m.n, dtype=torch.float64, device="cuda")
+    g = torch.empty((m.n, 3), dtype=torch.float64, device="cuda")
+    ctx.compute(x, r, a, g)
+    ctx.status_sync()
+    k0 = api.kernel_launches()
+    for _ in range(3):
+        ctx.compute(x, r, a, g)
+    ctx.status_sync()
+    assert api.kernel_launches() - k0 == 3 * 4
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_deterministic(api, torch_cuda, gen, precision):
     m = gen.globule(2000, 4)
     r1 = gpu_sasa(api, torch_cuda, m.coords, m.radii, precision)

@@ -31,3 +31,6 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     lib.dsasa_version.restype = ctypes.c_char_p
     assert b"sm_103a" in lib.dsasa_version()
+    # host-only diagnostics: no kernel has been launched by this process
+    lib.dsasa_kernel_launches.restype = ctypes.c_int64
+    assert lib.dsasa_kernel_launches() == 0
