@@ -45,6 +45,7 @@ struct dsasa_ctx {
     int* counts = nullptr;
     int* cstart = nullptr;
     int* blocksums = nullptr;
+    unsigned* bsync = nullptr;   // single-molecule build: partial boxes + ticket (zero between calls)
     long long* offsets = nullptr;
     int* defer = nullptr;       // atoms the fast kernel pass defers to the large pass
     unsigned char* cells = nullptr;   // per-atom cell records between the cell and terms kernels
@@ -99,7 +100,7 @@ template <class T> void dfree(T*& p) {
 
 void free_scratch(dsasa_ctx* c) {
     dfree(c->R); dfree(c->Rhl); dfree(c->f4); dfree(c->molid); dfree(c->rank); dfree(c->cell); dfree(c->sidx); dfree(c->sf4);
-    dfree(c->bbox); dfree(c->grids); dfree(c->counts); dfree(c->cstart); dfree(c->blocksums); dfree(c->offsets);
+    dfree(c->bbox); dfree(c->grids); dfree(c->counts); dfree(c->cstart); dfree(c->blocksums); dfree(c->bsync); dfree(c->offsets);
     dfree(c->defer); dfree(c->cells);
     dfree(c->nbl); dfree(c->nbn); dfree(c->ref_xyz); dfree(c->ref_rad); dfree(c->vstate);
     c->lists_n = 0;
@@ -134,7 +135,9 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
     if (e != cudaSuccess) { free_scratch(c); return cuda_fail(c, e, "cudaMalloc " #ptr); }
     ALLOC(R, na) ALLOC(Rhl, na) ALLOC(f4, na) ALLOC(molid, na) ALLOC(rank, na) ALLOC(cell, na) ALLOC(sidx, na) ALLOC(sf4, na)
     ALLOC(bbox, 8 * nm) ALLOC(grids, nm) ALLOC(counts, nc + 1) ALLOC(cstart, nc + 1) ALLOC(blocksums, nbs)
-    ALLOC(offsets, nm + 1) ALLOC(defer, na) ALLOC(cells, na * (int64_t)cell_record_bytes())
+    ALLOC(offsets, nm + 1) ALLOC(defer, na) ALLOC(cells, na * (int64_t)cell_record_bytes()) ALLOC(bsync, BUILD_SYNC_WORDS)
+    e = cudaMemsetAsync(c->bsync, 0, sizeof(unsigned) * BUILD_SYNC_WORDS, c->stream);
+    if (e != cudaSuccess) { free_scratch(c); return cuda_fail(c, e, "memset"); }
     if (c->cfg.skin > 0.0) {
         ALLOC(nbl, na * NBL_CAP) ALLOC(nbn, na) ALLOC(ref_xyz, 3 * na) ALLOC(ref_rad, na) ALLOC(vstate, 4)
         e = cudaMemsetAsync(c->vstate, 0, 4 * sizeof(int), c->stream);
@@ -162,7 +165,7 @@ cudaError_t build_cells(dsasa_ctx* c, const double* coords, const double* radii,
     b.max_cells = (int)c->cap_cells;
     b.R = c->R; b.Rhl = c->Rhl; b.f4 = c->f4; b.molid = c->molid; b.rank = c->rank; b.cell = c->cell;
     b.bbox = c->bbox; b.grids = c->grids; b.counts = c->counts; b.cstart = c->cstart; b.sidx = c->sidx;
-    b.sf4 = c->sf4; b.blocksums = c->blocksums; b.status = c->status; b.ncells_out = c->status + 1;
+    b.sf4 = c->sf4; b.blocksums = c->blocksums; b.sync = c->bsync; b.status = c->status; b.ncells_out = c->status + 1;
     return launch_build(b, c->stream);
 }
 

@@ -258,37 +258,48 @@ __global__ void k_scatter(BuildArgs a) {
     a.sf4[pos] = a.f4[i];
 }
 
-// The whole build for one molecule of at most kSmallAtoms atoms in one block of 1024 threads
-// (the multi-kernel path's launch overheads dominate at that size).  Same grid, same cells.
-constexpr int kSmallAtoms = 16384, kSmallT = 1024, kSmallCells = 8192;
+// The whole build for one molecule of at most kSmallAtoms atoms in one kernel (the
+// multi-kernel path's launch overheads dominate at that size).  Same grid, same cells.  One
+// thread per atom for the input pass (its FP64 work and conversions spread over several SMs);
+// each block leaves its partial bounding box in a.sync and takes a ticket, and the block that
+// takes the last ticket (nothing waits) finishes the build: box, grid, counting sort in shared
+// memory, scan, scatter.  It then resets the ticket for the next call.
+constexpr int kSmallAtoms = 16384, kSmallT = 1024, kSmallCells = 8192, kSmallBlocks = kSmallAtoms / kSmallT;
+static_assert(kSmallBlocks * 8 + 1 <= BUILD_SYNC_WORDS, "block-exchange area too small");
+__device__ __forceinline__ unsigned box_init(int k) {
+    return k < 3 ? fenc(INFINITY) : (k < 6 ? fenc(-INFINITY) : (k == 6 ? fenc(0.0f) : 0u));
+}
 __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
     if (a.skip && *a.skip) return;
     __shared__ unsigned bb[8];
     __shared__ MolGrid g;
     __shared__ int ws[kSmallT / 32];
     __shared__ int scount[kSmallCells];
+    __shared__ bool last;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (tid < 8) bb[tid] = tid < 3 ? fenc(INFINITY) : (tid < 6 ? fenc(-INFINITY) : (tid == 6 ? fenc(0.0f) : 0u));
+    if (tid < 8) bb[tid] = box_init(tid);
     __syncthreads();
     unsigned lo[3] = {fenc(INFINITY), fenc(INFINITY), fenc(INFINITY)};
     unsigned hi[4] = {fenc(-INFINITY), fenc(-INFINITY), fenc(-INFINITY), fenc(0.0f)};
-#pragma unroll 4
-    for (int i = tid; i < a.n; i += kSmallT) {
-        double x = a.xyz[3 * i], y = a.xyz[3 * i + 1], z = a.xyz[3 * i + 2];
-        double R = a.radii[i] + a.probe;
-        if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(R)) || !(R > 0.0)) {
-            atomicOr(a.status, ST_INPUT);
-            x = y = z = 0.0;
-            R = 1.0;
+    {
+        const int i = blockIdx.x * kSmallT + tid;
+        if (i < a.n) {
+            double x = a.xyz[3 * i], y = a.xyz[3 * i + 1], z = a.xyz[3 * i + 2];
+            double R = a.radii[i] + a.probe;
+            if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(R)) || !(R > 0.0)) {
+                atomicOr(a.status, ST_INPUT);
+                x = y = z = 0.0;
+                R = 1.0;
+            }
+            a.R[i] = R;
+            { float h = (float)R; a.Rhl[i] = make_float2(h, (float)(R - (double)h)); }
+            a.molid[i] = 0;
+            float4 f = make_float4((float)x, (float)y, (float)z, (float)R);
+            a.f4[i] = f;
+            unsigned e[4] = {fenc(f.x), fenc(f.y), fenc(f.z), fenc(f.w)};
+            for (int k = 0; k < 3; ++k) { lo[k] = min(lo[k], e[k]); hi[k] = max(hi[k], e[k]); }
+            hi[3] = max(hi[3], e[3]);
         }
-        a.R[i] = R;
-        { float h = (float)R; a.Rhl[i] = make_float2(h, (float)(R - (double)h)); }
-        a.molid[i] = 0;
-        float4 f = make_float4((float)x, (float)y, (float)z, (float)R);
-        a.f4[i] = f;
-        unsigned e[4] = {fenc(f.x), fenc(f.y), fenc(f.z), fenc(f.w)};
-        for (int k = 0; k < 3; ++k) { lo[k] = min(lo[k], e[k]); hi[k] = max(hi[k], e[k]); }
-        hi[3] = max(hi[3], e[3]);
     }
     for (int k = 0; k < 3; ++k) {
         lo[k] = __reduce_min_sync(0xffffffffu, lo[k]);
@@ -299,6 +310,24 @@ __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
         for (int k = 0; k < 3; ++k) { atomicMin(&bb[k], lo[k]); atomicMax(&bb[3 + k], hi[k]); }
         atomicMax(&bb[6], hi[3]);
     }
+    __syncthreads();
+    // partial box out, every thread's writes made visible, then the ticket
+    if (tid < 8) a.sync[8 * blockIdx.x + tid] = bb[tid];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(a.sync + 8 * kSmallBlocks, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (tid < 8) {
+        unsigned v = box_init(tid);
+        for (int b = 0; b < (int)gridDim.x; ++b) {
+            const unsigned p = __ldcg(a.sync + 8 * b + tid);
+            v = tid < 3 ? min(v, p) : (tid < 7 ? max(v, p) : 0u);
+        }
+        bb[tid] = v;
+    }
+    if (tid == 0) a.sync[8 * kSmallBlocks] = 0u;   // ticket back to zero for the next call
     __syncthreads();
     if (tid == 0) {
         MolGrid gg = make_grid(bb, a.n, a.skin);
@@ -319,7 +348,7 @@ __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
     __syncthreads();
 #pragma unroll 4
     for (int i = tid; i < a.n; i += kSmallT) {
-        int c = cell_of(g, a.f4[i]);
+        int c = cell_of(g, __ldcg(a.f4 + i));   // written by other blocks of this grid
         if (c >= a.max_cells) c = a.max_cells - 1;   // only after a reported overflow
         a.cell[i] = c;
         a.rank[i] = atomicAdd(&cnt[c], 1);
@@ -359,7 +388,7 @@ __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
     for (int i = tid; i < a.n; i += kSmallT) {
         int pos = (sm ? cnt[a.cell[i]] : a.cstart[a.cell[i]]) + a.rank[i];
         a.sidx[pos] = i;
-        a.sf4[pos] = a.f4[i];
+        a.sf4[pos] = __ldcg(a.f4 + i);
     }
 }
 
@@ -434,7 +463,7 @@ cudaError_t launch_verlet_check(const double* xyz, const double* radii, const do
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     if (a.n_mol == 1 && a.n <= kSmallAtoms) {
-        k_build_small<<<1, kSmallT, 0, s>>>(a);
+        k_build_small<<<(a.n + kSmallT - 1) / kSmallT, kSmallT, 0, s>>>(a);
         note_launches(1);
         return cudaGetLastError();
     }

@@ -8,6 +8,10 @@ namespace dsasa {
 // host: adds k to the library-wide count of kernel launches (dsasa_kernel_launches)
 void note_launches(int k);
 
+// words of the single-molecule cell-list build's block-exchange area: 16 partial bounding
+// boxes of 8 words, then the completion ticket
+constexpr int BUILD_SYNC_WORDS = 16 * 8 + 1;
+
 // device status bits (ORed by kernels, read by dsasa_status_sync)
 enum : int {
     ST_CAND_OVF = 1,      // more overlapping neighbours than one warp's candidate table holds
@@ -55,6 +59,7 @@ struct BuildArgs {
     int* sidx;         // n
     float4* sf4;       // n
     int* blocksums;    // scan scratch
+    unsigned* sync;    // BUILD_SYNC_WORDS, zero between calls: single-molecule build's partial boxes + ticket
     int* status;
     int* ncells_out;   // device int: total cells used
 };

@@ -40,7 +40,8 @@ constexpr size_t OFF_CSTART = al(OFF_COUNTS + sizeof(int) * (kMaxCells + 1));
 constexpr size_t OFF_BSUM = al(OFF_CSTART + sizeof(int) * (kMaxCells + 1));
 constexpr size_t OFF_DEFER = al(OFF_BSUM + sizeof(int) * 4096);
 constexpr size_t OFF_STATUS = al(OFF_DEFER + sizeof(int) * kMaxAtoms);
-constexpr size_t kScratchBytes = al(OFF_STATUS + sizeof(int) * 4);
+constexpr size_t OFF_SYNC = al(OFF_STATUS + sizeof(int) * 4);   // zero at load; the build leaves it zero
+constexpr size_t kScratchBytes = al(OFF_SYNC + sizeof(unsigned) * BUILD_SYNC_WORDS);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -98,6 +99,7 @@ extern "C" dsasa_status dsasa_compute_noalloc(const double* coords, const double
     b.counts = (int*)(base + OFF_COUNTS);
     b.cstart = (int*)(base + OFF_CSTART);
     b.blocksums = (int*)(base + OFF_BSUM);
+    b.sync = (unsigned*)(base + OFF_SYNC);
     b.status = status;
     b.ncells_out = status + 1;
     if (launch_build(b, s) != cudaSuccess) return DSASA_ERR_CUDA;
