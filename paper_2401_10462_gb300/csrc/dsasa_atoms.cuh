@@ -345,6 +345,8 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
     const int wib = threadIdx.x >> 5;
     Smem<R, NE, NT>* S = &smem_all[wib];
     const int nwarps = gridDim.x * WARPS;
+    grid_dep_trigger();
+    grid_dep_wait();   // the previous kernel of the call (cell list, cell records) is complete
     const int total = deferred ? *A.work_count : A.n;
 
     for (int s0 = blockIdx.x * WARPS + wib; s0 < total; s0 += nwarps) {
@@ -1330,7 +1332,8 @@ template <class R> bool cells_in_one_wave(int n) {
 
 // Fast pass (64 planes, 64 vertex slots) over all atoms: with a cell store, the cell,
 // classification and terms kernels, else the fused kernel.  The atoms it defers get the fused 128 / 128
-// pass, whose grid reads the deferred count from device memory (no host sync).
+// pass, whose grid reads the deferred count from device memory (no host sync).  The deferred
+// count must be zero when the first kernel starts (the cell-list build clears it).
 template <class R>
 cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
@@ -1347,45 +1350,48 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     fast.ev = big.ev = nullptr;
     // the deferred atoms are few: a small grid that loops over them (most calls have none)
     int big_blocks = blocks < 64 ? blocks : 64;
-    if (a.defer_count) cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
     const bool g = grad && a.rec == nullptr;
     auto mark = [&](int k) {
         if (a.ev) cudaEventRecord(a.ev[k], s);
     };
+    // every kernel after the cell-list build is a programmatic dependent launch in the mixed
+    // form (measured: 3 % faster on a 5k-atom molecule); the all-FP64 form's kernels ran 3 %
+    // slower that way and are launched in plain stream order
+    cudaError_t err = cudaSuccess;
+    auto go = [&](auto kernel, int grid, int block, const AtomArgs& args) {
+        cudaError_t e = launch_dependent(kernel, grid, block, s, sizeof(R) == 4, args);
+        if (err == cudaSuccess) err = e;
+        note_launches(1);
+    };
     if (a.cells) {
         auto nb = [&](int w) { return (a.n + w - 1) / w; };
         if (cells_in_one_wave<R>(a.n)) {
-            k_atoms<R, false, 64, 64, PH_CC><<<nb(WARPS_CELL), WARPS_CELL * 32, 0, s>>>(fast);
-            note_launches(1);
+            go(k_atoms<R, false, 64, 64, PH_CC>, nb(WARPS_CELL), WARPS_CELL * 32, fast);
             mark(0);
             mark(1);
         } else {
-            k_atoms<R, false, 64, 64, PH_CELL><<<nb(WARPS_CELL), WARPS_CELL * 32, 0, s>>>(fast);
+            go(k_atoms<R, false, 64, 64, PH_CELL>, nb(WARPS_CELL), WARPS_CELL * 32, fast);
             mark(0);
-            k_atoms<R, false, 64, 64, PH_CLASS><<<nb(WARPS_CLASS), WARPS_CLASS * 32, 0, s>>>(fast);
-            note_launches(2);
+            go(k_atoms<R, false, 64, 64, PH_CLASS>, nb(WARPS_CLASS), WARPS_CLASS * 32, fast);
             mark(1);
         }
-        if (g) k_atoms<R, true, 64, 64, PH_TERMS><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
-        else k_atoms<R, false, 64, 64, PH_TERMS><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
-        if (a.vol) k_atoms<R, false, 64, 64, PH_VOL><<<nb(WARPS_TERMS), WARPS_TERMS * 32, 0, s>>>(fast);
-        note_launches(a.vol ? 2 : 1);
+        if (g) go(k_atoms<R, true, 64, 64, PH_TERMS>, nb(WARPS_TERMS), WARPS_TERMS * 32, fast);
+        else go(k_atoms<R, false, 64, 64, PH_TERMS>, nb(WARPS_TERMS), WARPS_TERMS * 32, fast);
+        if (a.vol) go(k_atoms<R, false, 64, 64, PH_VOL>, nb(WARPS_TERMS), WARPS_TERMS * 32, fast);
         mark(2);
     } else {
-        if (g) k_atoms<R, true, 64, 64, PH_ALL><<<blocks, WARPS * 32, 0, s>>>(fast);
-        else k_atoms<R, false, 64, 64, PH_ALL><<<blocks, WARPS * 32, 0, s>>>(fast);
-        note_launches(1);
+        if (g) go(k_atoms<R, true, 64, 64, PH_ALL>, blocks, WARPS * 32, fast);
+        else go(k_atoms<R, false, 64, 64, PH_ALL>, blocks, WARPS * 32, fast);
         mark(0);
         mark(1);
         mark(2);
     }
     if (a.defer_list) {
-        if (g) k_atoms<R, true, 128, 128, PH_ALL><<<big_blocks, WARPS * 32, 0, s>>>(big);
-        else k_atoms<R, false, 128, 128, PH_ALL><<<big_blocks, WARPS * 32, 0, s>>>(big);
-        note_launches(1);
+        if (g) go(k_atoms<R, true, 128, 128, PH_ALL>, big_blocks, WARPS * 32, big);
+        else go(k_atoms<R, false, 128, 128, PH_ALL>, big_blocks, WARPS * 32, big);
     }
     mark(3);
-    return cudaGetLastError();
+    return err != cudaSuccess ? err : cudaGetLastError();
 }
 #endif
 

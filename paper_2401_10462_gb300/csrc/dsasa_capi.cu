@@ -152,7 +152,8 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
 
 // the cell list of the inputs in the context's scratch (enqueued on its stream)
 cudaError_t build_cells(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n, int n_mol,
-                        const long long* offsets_dev, const int* skip = nullptr) {
+                        const long long* offsets_dev, const int* skip = nullptr,
+                        int* zero_word = nullptr) {
     BuildArgs b{};
     b.skip = skip;
     b.xyz = coords;
@@ -165,7 +166,7 @@ cudaError_t build_cells(dsasa_ctx* c, const double* coords, const double* radii,
     b.max_cells = (int)c->cap_cells;
     b.R = c->R; b.Rhl = c->Rhl; b.f4 = c->f4; b.molid = c->molid; b.rank = c->rank; b.cell = c->cell;
     b.bbox = c->bbox; b.grids = c->grids; b.counts = c->counts; b.cstart = c->cstart; b.sidx = c->sidx;
-    b.sf4 = c->sf4; b.blocksums = c->blocksums; b.sync = c->bsync; b.status = c->status; b.ncells_out = c->status + 1;
+    b.sf4 = c->sf4; b.blocksums = c->blocksums; b.sync = c->bsync; b.zero_word = zero_word; b.status = c->status; b.ncells_out = c->status + 1;
     return launch_build(b, c->stream);
 }
 
@@ -184,7 +185,9 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
                                                c->vstate, c->stream);
         if (ev_e != cudaSuccess) return cuda_fail(c, ev_e, "Verlet check launch");
     }
-    cudaError_t e = build_cells(c, coords, radii, probe, n, n_mol, offsets_dev, lists ? c->vstate + 2 : nullptr);
+    // the build also clears the deferred-atom count of the atom kernels that follow it
+    cudaError_t e = build_cells(c, coords, radii, probe, n, n_mol, offsets_dev, lists ? c->vstate + 2 : nullptr,
+                                c->status + 2);
     if (e != cudaSuccess) return cuda_fail(c, e, "cell-list launch");
     if (ev) cudaEventRecord(ev[1], c->stream);
     AtomArgs a{};

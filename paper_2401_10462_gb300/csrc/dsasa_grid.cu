@@ -22,8 +22,9 @@ __device__ __forceinline__ float fdec(unsigned u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-__global__ void k_bbox_init(unsigned* bbox, int n_mol) {
+__global__ void k_bbox_init(unsigned* bbox, int n_mol, int* zero_word) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m == 0 && zero_word) *zero_word = 0;
     if (m >= n_mol) return;
     unsigned lo = fenc(INFINITY), hi = fenc(-INFINITY);
     for (int k = 0; k < 3; ++k) { bbox[8 * m + k] = lo; bbox[8 * m + 3 + k] = hi; }
@@ -250,6 +251,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(const int* in, int len, co
 }
 
 __global__ void k_scatter(BuildArgs a) {
+    grid_dep_trigger();
     if (a.skip && *a.skip) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
@@ -270,6 +272,8 @@ __device__ __forceinline__ unsigned box_init(int k) {
     return k < 3 ? fenc(INFINITY) : (k < 6 ? fenc(-INFINITY) : (k == 6 ? fenc(0.0f) : 0u));
 }
 __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.zero_word) *a.zero_word = 0;
+    grid_dep_trigger();
     if (a.skip && *a.skip) return;
     __shared__ unsigned bb[8];
     __shared__ MolGrid g;
@@ -395,7 +399,7 @@ __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
 cudaError_t launch_build_multi(const BuildArgs& a, cudaStream_t s) {
     const int T = 256;
     int nb = (a.n + T - 1) / T;
-    k_bbox_init<<<(a.n_mol + T - 1) / T, T, 0, s>>>(a.bbox, a.n_mol);
+    k_bbox_init<<<(a.n_mol + T - 1) / T, T, 0, s>>>(a.bbox, a.n_mol, a.zero_word);
     k_prep<<<nb, T, 0, s>>>(a);
     k_grid_local<<<(a.n_mol + T - 1) / T, T, 0, s>>>(a);
     k_grid_scan<<<1, 1024, 0, s>>>(a);

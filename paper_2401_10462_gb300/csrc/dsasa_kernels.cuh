@@ -3,7 +3,34 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace dsasa {
+
+// Programmatic dependent launch (the kernels of one call run back to back on one stream): a
+// kernel launched by launch_dependent may be scheduled while the previous kernel of the
+// stream is still running; it calls grid_dep_wait() before it touches anything, which returns
+// once that kernel has completed and its writes are visible.  grid_dep_trigger() lets the
+// next kernel be scheduled once every block of this one has started.  Both are no-ops for a
+// kernel launched without the attribute.
+#ifdef __CUDACC__
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+template <class... K, class... A>
+cudaError_t launch_dependent(void (*kernel)(K...), int grid, int block, cudaStream_t s, bool early, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = early ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 // host: adds k to the library-wide count of kernel launches (dsasa_kernel_launches)
 void note_launches(int k);
@@ -44,6 +71,7 @@ struct BuildArgs {
     const long long* offsets;   // device, n_mol + 1 (NULL: one molecule)
     double skin;
     const int* skip;   // non-NULL and *skip != 0: the previous cell list is reused (nothing to do)
+    int* zero_word;    // non-NULL: set to 0 by the build's first kernel (the next atom kernels' deferred count)
     int max_cells;
     // outputs / scratch
     double* R;         // n
@@ -87,7 +115,7 @@ struct AtomArgs {
     // deferral: the fast pass appends sorted positions it cannot hold to defer_list; the
     // large pass reads work_list[0 .. *work_count)
     int* defer_list;
-    int* defer_count;
+    int* defer_count;       // zero when the first atom kernel starts (cleared by the cell-list build)
     const int* work_list;
     const int* work_count;
     // per-atom cell records (by sorted position) between the cell kernel and the terms

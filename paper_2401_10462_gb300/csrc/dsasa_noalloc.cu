@@ -100,6 +100,7 @@ extern "C" dsasa_status dsasa_compute_noalloc(const double* coords, const double
     b.cstart = (int*)(base + OFF_CSTART);
     b.blocksums = (int*)(base + OFF_BSUM);
     b.sync = (unsigned*)(base + OFF_SYNC);
+    b.zero_word = status + 2;   // the deferred count of the atom kernels
     b.status = status;
     b.ncells_out = status + 1;
     if (launch_build(b, s) != cudaSuccess) return DSASA_ERR_CUDA;
