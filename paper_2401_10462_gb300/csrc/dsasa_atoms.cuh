@@ -374,11 +374,18 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         int nc = 0;
         int nrounds = 1;     // vertex-slot rounds in use: slots < 32 * nrounds (warp-uniform)
         // per-lane vertex caches (homogeneous z = Dv / D with magnitudes for the filter)
-        R V[SPL][4], Va[SPL][4];
+        // (V).  FP32 form: for a first loose filter, the sum of the four filter magnitudes (Vs,
+        // rounded up); a test that the loose bound leaves open recomputes the magnitudes.  FP64
+        // form: the four magnitudes (Va; measured faster there).
+        constexpr bool LOOSE = sizeof(R) == 4;
+        R V[SPL][4], Vs[SPL], Va[SPL][LOOSE ? 1 : 4];
         unsigned alive = 0;
         auto compute_vertex = [&](int r, int t) {
             VtxFA<R> q = vertex_fa(S, S->tv[t]);
-            for (int k = 0; k < 4; ++k) { V[r][k] = q.v[k]; Va[r][k] = q.a[k]; }
+            for (int k = 0; k < 4; ++k) V[r][k] = q.v[k];
+            if constexpr (LOOSE) Vs[r] = ((q.a[0] + q.a[1]) + (q.a[2] + q.a[3])) * (R)1.000001;
+            else
+                for (int k = 0; k < 4; ++k) Va[r][k] = q.a[k];
         };
 
         // molecular volume of the atom from its classified cell (lane 0 writes)
@@ -627,6 +634,8 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         for (int kk = 0; kk < nc && !empty; ++kk) {
             const int m = S->ord[kk] & (NE - 1);
             const PlaneN<FA<R>> M = fplane(S, m);
+            // sum_k |q_k| a_k <= max_k |q_k| * sum_k a_k: the loose magnitude of the clip test
+            const R qmax = fmax(fmax(M.q.x.a, M.q.y.a), fmax(M.q.z.a, M.b.a));
             unsigned remv = 0;
 #pragma unroll
             for (int r = 0; r < SPL; ++r) {
@@ -634,12 +643,19 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 if (!(alive >> r & 1)) continue;
                 FA<R> sv;
                 sv.v = M.q.x.v * V[r][0] + M.q.y.v * V[r][1] + M.q.z.v * V[r][2] - M.b.v * V[r][3];
-                sv.a = M.q.x.a * Va[r][0] + M.q.y.a * Va[r][1] + M.q.z.a * Va[r][2] + M.b.a * Va[r][3];
+                if constexpr (LOOSE) sv.a = qmax * Vs[r];
+                else sv.a = M.q.x.a * Va[r][0] + M.q.y.a * Va[r][1] + M.q.z.a * Va[r][2] + M.b.a * Va[r][3];
                 int sg = fa_sign(sv, Gam<R>::gclip, Gam<R>::tiny);
+                if (LOOSE && sg == 0) {
+                    const uchar4 v = S->tv[r * 32 + lane];
+                    const VtxFA<R> q = vertex_fa(S, v);
+                    sv.a = M.q.x.a * q.a[0] + M.q.y.a * q.a[1] + M.q.z.a * q.a[2] + M.b.a * q.a[3];
+                    sg = fa_sign(sv, Gam<R>::gclip, Gam<R>::tiny);
+                }
                 if (sg == 0) {
-                    uchar4 v = S->tv[r * 32 + lane];
-                    sg = resolve_exact(c, PK_CLIP, S->pg[v.x & (NE - 1)], S->pg[v.y & (NE - 1)], S->pg[v.z & (NE - 1)],
-                                       S->pg[m], Gam<R>::try64);
+                    const uchar4 v = S->tv[r * 32 + lane];
+                    sg = resolve_exact(c, PK_CLIP, S->pg[v.x & (NE - 1)], S->pg[v.y & (NE - 1)],
+                                       S->pg[v.z & (NE - 1)], S->pg[m], Gam<R>::try64);
                 }
                 if (sg > 0) remv |= 1u << r;
             }
@@ -878,8 +894,15 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 else {
                     FA<R> P;
                     P.v = V[r][0] * V[r][0] + V[r][1] * V[r][1] + V[r][2] * V[r][2] - wi.v * V[r][3] * V[r][3];
-                    P.a = Va[r][0] * Va[r][0] + Va[r][1] * Va[r][1] + Va[r][2] * Va[r][2] + wi.a * Va[r][3] * Va[r][3];
+                    // sum_k a_k^2 + w a_3^2 <= max(1, w) (sum_k a_k)^2 (loose), then the magnitudes
+                    if constexpr (LOOSE) P.a = fmax((R)1, wi.a) * Vs[r] * Vs[r] * (R)1.000001;
+                    else P.a = Va[r][0] * Va[r][0] + Va[r][1] * Va[r][1] + Va[r][2] * Va[r][2] + wi.a * Va[r][3] * Va[r][3];
                     int sg = fa_sign(P, Gam<R>::g, Gam<R>::tiny);
+                    if (LOOSE && sg == 0) {
+                        const VtxFA<R> q = vertex_fa(S, v);
+                        P.a = q.a[0] * q.a[0] + q.a[1] * q.a[1] + q.a[2] * q.a[2] + wi.a * q.a[3] * q.a[3];
+                        sg = fa_sign(P, Gam<R>::g, Gam<R>::tiny);
+                    }
                     if (sg == 0) sg = resolve_exact(c, PK_TET, S->pg[v.x], S->pg[v.y], S->pg[v.z], 0, Gam<R>::try64);
                     f = sg <= 0 ? 1 : 0;
                     if (f) kmask |= 1u << r;
