@@ -63,11 +63,13 @@ template <class R, int NE, int NT> struct Smem {
     R pB[NE];             // magnitude proxy of b for the filters
     int pg[NE];           // global atom index (>= 0) or -1 - ghost id
     uint8_t start[NE];    // a vertex slot on the face of this plane
-    uint8_t bnext[NE], bprev[NE], bslot[NE], bkept[NE], bkedge[NE];
+    // boundary edges of the current cut, by number: (a, b, kept neighbour slot, new slot, edge
+    // index in the kept neighbour) packed 7/7/7/7/2 bits; the new slot by first and last plane
+    unsigned bedge[NE];
+    uint8_t bslot[NE], eslot[NE];
     uint8_t ord[NE];      // clipping order (entry ids)
     uint8_t eflag[NE];    // face summary: bit0 edge in C, bit1 interior (closed)
     R ephi[NE];           // Phi_ia of the face
-    uint8_t blist[NE];    // boundary edges of the current cut (their first plane id)
     uchar4 tv[NT];        // cell vertex = triangle of plane ids (x = NONE: dead slot)
     uchar4 ta[NT];        // neighbour slots across edges (v0 v1), (v1 v2), (v2 v0)
     uint8_t kf[NT];       // 0 not in C, 1 tetrahedron of C, 2 involves a ghost plane
@@ -211,12 +213,16 @@ template <class SM, class R = typename SM::Real> __device__ __forceinline__ Plan
 }
 // homogeneous cell vertex (Dv, D) of the planes of triangle v, with magnitudes for the filter
 template <class R> struct VtxFA { R v[4], a[4]; };
-template <class SM, class R = typename SM::Real> __device__ __noinline__ VtxFA<R> vertex_fa(const SM* S, uchar4 v) {
+template <class SM, class R = typename SM::Real> __device__ __forceinline__ VtxFA<R> vertex_fa_inl(const SM* S, uchar4 v) {
     PlaneN<FA<R>> Pa = fplane(S, v.x), Pb = fplane(S, v.y), Pc = fplane(S, v.z);
     V3<FA<R>> Dv;
     FA<R> D;
     vertex_hom(Pa, Pb, Pc, Dv, D);
     return {{Dv.x.v, Dv.y.v, Dv.z.v, D.v}, {Dv.x.a, Dv.y.a, Dv.z.a, D.a}};
+}
+// out of line (the kernels that also classify or evaluate terms keep their code small)
+template <class SM, class R = typename SM::Real> __device__ __noinline__ VtxFA<R> vertex_fa(const SM* S, uchar4 v) {
+    return vertex_fa_inl(S, v);
 }
 // Volume pieces of the restricted cell (molecular volume, the paper's named extension).  For
 // every face f of the cell (plane q_f . z = b_f, unit normal u_f, signed distance h_f from
@@ -381,7 +387,11 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         R V[SPL][4], Vs[SPL], Va[SPL][LOOSE ? 1 : 4];
         unsigned alive = 0;
         auto compute_vertex = [&](int r, int t) {
-            VtxFA<R> q = vertex_fa(S, S->tv[t]);
+            // inline in the split cell and classification kernels (measured faster there), a
+            // call in the kernels that hold more code
+            VtxFA<R> q;
+            if constexpr (PH == PH_CELL || PH == PH_CLASS) q = vertex_fa_inl(S, S->tv[t]);
+            else q = vertex_fa(S, S->tv[t]);
             for (int k = 0; k < 4; ++k) V[r][k] = q.v[k];
             if constexpr (LOOSE) Vs[r] = ((q.a[0] + q.a[1]) + (q.a[2] + q.a[3])) * (R)1.000001;
             else
@@ -533,17 +543,24 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         for (int k = 2; k <= ns; k <<= 1) {
             for (int j = k >> 1; j > 0; j >>= 1) {
                 if (j >= 32) {
-                    int jr = j >> 5;
+                    // rounds r and r ^ (j / 32) in this lane's registers (the partner round is
+                    // a compile-time index in every unrolled branch, so key and pay stay in
+                    // registers)
+                    const int jr = j >> 5;
 #pragma unroll
-                    for (int r = 0; r < SPL; ++r) {
-                        int r2 = r ^ jr;
-                        if (r2 > r && r2 < nsr) {
-                            int e = r * 32 + lane;
-                            bool up = (e & k) == 0;
-                            bool sw = up ? (key[r] > key[r2]) : (key[r] < key[r2]);
-                            if (sw) {
-                                unsigned long long tk = key[r]; key[r] = key[r2]; key[r2] = tk;
-                                unsigned tp = pay[r]; pay[r] = pay[r2]; pay[r2] = tp;
+                    for (int JR = 1; JR < SPL; JR <<= 1) {
+                        if (jr != JR) continue;
+#pragma unroll
+                        for (int r = 0; r < SPL; ++r) {
+                            const int r2 = r ^ JR;
+                            if (r2 > r && r2 < nsr) {
+                                int e = r * 32 + lane;
+                                bool up = (e & k) == 0;
+                                bool sw = up ? (key[r] > key[r2]) : (key[r] < key[r2]);
+                                if (sw) {
+                                    unsigned long long tk = key[r]; key[r] = key[r2]; key[r2] = tk;
+                                    unsigned tp = pay[r]; pay[r] = pay[r2]; pay[r2] = tp;
+                                }
                             }
                         }
                     }
@@ -715,12 +732,10 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                         int x = e - nrem;
                         slot = x < nfree ? S->fs[nfree - 1 - x] : hw + (x - nfree);
                     }
-                    S->blist[e & (NE - 1)] = a;
-                    S->bnext[a] = b;
-                    S->bprev[b] = a;
-                    S->bkept[a] = t2;
-                    S->bkedge[a] = k2;
-                    S->bslot[a] = (uint8_t)slot;
+                    S->bedge[e & (NE - 1)] = (unsigned)a | ((unsigned)b << 7) | ((unsigned)t2 << 14) |
+                                             ((unsigned)(slot & 127) << 21) | ((unsigned)k2 << 28);
+                    S->bslot[a] = (uint8_t)slot;   // the new triangle on the edge that starts at a
+                    S->eslot[b] = (uint8_t)slot;   // ... and ends at b
                 }
                 nb += __popc(bb);
             }
@@ -733,16 +748,16 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             }
             __syncwarp();
             for (int e = lane; e < nb; e += 32) {
-                uint8_t a = S->blist[e];
-                uint8_t b = S->bnext[a];
-                int sl = S->bslot[a] & (NT - 1);
+                const unsigned w = S->bedge[e];
+                const uint8_t a = w & 127, b = (w >> 7) & 127, t2 = (w >> 14) & 127;
+                const int sl = (w >> 21) & (NT - 1);
                 S->tv[sl] = make_uchar4(a, b, (uint8_t)m, 0);
-                S->ta[sl] = make_uchar4(S->bkept[a], S->bslot[b & (NE - 1)], S->bslot[S->bprev[a] & (NE - 1)], 0);
-                ta_set(S, S->bkept[a], S->bkedge[a] & 3, (uint8_t)sl);
+                S->ta[sl] = make_uchar4(t2, S->bslot[b & (NE - 1)], S->eslot[a & (NE - 1)], 0);
+                ta_set(S, t2, (w >> 28) & 3, (uint8_t)sl);
                 S->start[a] = (uint8_t)sl;
                 S->rem[sl] = 2;
             }
-            if (lane == 0) S->start[m] = S->bslot[S->blist[0]];
+            if (lane == 0) S->start[m] = (uint8_t)((S->bedge[0] >> 21) & (NT - 1));
             __syncwarp();
             // leftover removed slots become free; update the slot allocator
             if (extra < 0) {
