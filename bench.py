@@ -114,7 +114,7 @@ class ClockSampler:
 def kernel_sha() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("dsasa_atoms.cuh", "dsasa_math.cuh"):
+    for f in ("dsasa_atoms.cuh", "dsasa_math.cuh", "dsasa_kernels.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2401_10462_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
