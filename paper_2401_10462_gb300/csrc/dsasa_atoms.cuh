@@ -1208,8 +1208,13 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             }
         }
         __syncwarp();
-        for (int e = lane; e < ntl; e += 32) {
+        // With the gradient, four lanes per exterior triangle: parts 0-2 evaluate the lens
+        // gradient of owner i, a or b (one call on all those lanes), part 3 the area term; part
+        // 0 adds the wing dihedral term when one tetrahedron of C holds the triangle.
+        constexpr int GT = GRAD ? 4 : 1;
+        for (int j = lane; j < GT * ntl; j += 32) {
             {
+                const int e = j / GT, part = GRAD ? (j & 3) : 3;
                 const int t = S->tl[e] >> 2, k = S->tl[e] & 3;
                 uchar4 v = S->tv[t];
                 uint8_t a = tv_get(v, k), b = tv_get(v, (k + 1) % 3), cc = tv_get(v, (k + 2) % 3);
@@ -1222,37 +1227,40 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 if constexpr (FFM) {
                     const float2 ra2 = A.Rhl[ga], rb2 = A.Rhl[gb];
                     const FF Ra = {ra2.x, ra2.y}, Rb = {rb2.x, rb2.y};
-                    FF v = tri_term_ff_ol(pa, pb, Ri_ff, Ra, Rb, Ri2_ff);
-                    acc_ff = ff_add(acc_ff, FF{cff * v.h, cff * v.l});
-                    cf_sum += cff;
+                    if (part == 3) {
+                        FF v = tri_term_ff_ol(pa, pb, Ri_ff, Ra, Rb, Ri2_ff);
+                        acc_ff = ff_add(acc_ff, FF{cff * v.h, cff * v.l});
+                        cf_sum += cff;
+                    }
                     Raf = Ra.h;
                     Rbf = Rb.h;
                     dRab = ff_mul(ff_sub(Ra, Rb), ff_add(Ra, Rb)).h;
                 } else {
                     const double Ra = A.R[ga], Rb = A.R[gb];
-                    area_acc += (double)cff * tri_term_mixed_ol(pa, pb, c.Ri, Ra, Rb);
+                    if (part == 3) area_acc += (double)cff * tri_term_mixed_ol(pa, pb, c.Ri, Ra, Rb);
                     Raf = (R)Ra;
                     Rbf = (R)Rb;
                     dRab = (R)((Ra - Rb) * (Ra + Rb));
                 }
-                if (GRAD) {
+                if (GRAD && part < 3) {
                     const P3<R> O = {zero, zero, zero};
                     const R waf = (R)(A.w ? A.w[ga] : 1.0), wbf = (R)(A.w ? A.w[gb] : 1.0);
-                    // owner i: d/dp_i = -(g2 + g3)
-                    P3x2<R> lg = lens_grad_ol(pa, pb, Rr, Raf, Rbf);
-                    R sx = -wif * (lg.a.x + lg.b.x), sy = -wif * (lg.a.y + lg.b.y), sz = -wif * (lg.a.z + lg.b.z);
-                    // owner a: p_i is the second centre
-                    lg = lens_grad_ol(O - pa, pb - pa, Raf, Rr, Rbf);
-                    sx += waf * lg.a.x; sy += waf * lg.a.y; sz += waf * lg.a.z;
-                    // owner b
-                    lg = lens_grad_ol(O - pb, pa - pb, Rbf, Rr, Raf);
-                    sx += wbf * lg.a.x; sy += wbf * lg.a.y; sz += wbf * lg.a.z;
-                    sx *= cff; sy *= cff; sz *= cff;
-                    if (nk == 1) {
+                    // owner i: d/dp_i = -(g2 + g3); owner a: p_i is the second centre; owner b
+                    const P3<R> u = part == 0 ? pa : (part == 1 ? O - pa : O - pb);
+                    const P3<R> w = part == 0 ? pb : (part == 1 ? pb - pa : pa - pb);
+                    const R r0 = part == 0 ? Rr : (part == 1 ? Raf : Rbf);
+                    const R r1 = part == 0 ? Raf : Rr;
+                    const R r2 = part == 2 ? Raf : Rbf;
+                    const P3x2<R> lg = lens_grad_ol(u, w, r0, r1, r2);
+                    const R f = cff * (part == 0 ? -wif : (part == 1 ? waf : wbf));
+                    R sx = f * (part == 0 ? lg.a.x + lg.b.x : lg.a.x);
+                    R sy = f * (part == 0 ? lg.a.y + lg.b.y : lg.a.y);
+                    R sz = f * (part == 0 ? lg.a.z + lg.b.z : lg.a.z);
+                    if (part == 0 && nk == 1) {
                         // the single tetrahedron of C on this triangle: (i, a, b, x); its
                         // orientation is + when it is the cell vertex t, - when it is t2
-                        uchar4 w = S->tv[t2];
-                        uint8_t xo = (w.x != a && w.x != b) ? w.x : ((w.y != a && w.y != b) ? w.y : w.z);
+                        uchar4 w2 = S->tv[t2];
+                        uint8_t xo = (w2.x != a && w2.x != b) ? w2.x : ((w2.y != a && w2.y != b) ? w2.y : w2.z);
                         bool on_t = S->kf[t] == 1;
                         uint8_t x = on_t ? cc : xo;
                         const R dab = norm3(pb - pa), inv2 = (R)0.5 / dab;

@@ -206,6 +206,32 @@ def test_one_wave_and_split_kernels_agree(api, torch_cuda, orc, gen, precision):
     check_grad(g1, rg)
 
 
+def test_single_molecule_build_sizes(api, torch_cuda, gen):
+    """The single-molecule cell-list build runs ceil(n / 1024) blocks whose last block finishes
+    the sort (and resets its ticket); sizes at the block and kernel-choice boundaries, computed
+    one after another on one context, equal the multi-molecule build's results (a batch with a
+    2-atom molecule far away takes the multi-kernel build)."""
+    torch = torch_cuda
+    ctx = api.Context()
+    for n in (1, 1023, 1024, 1025, 4097, 16384, 16385, 3000):
+        m = gen.globule(n, 20 + n % 7)
+        x, r = _dev(torch, m.coords), _dev(torch, m.radii)
+        a = torch.empty(n, dtype=torch.float64, device="cuda")
+        g = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        ctx.compute(x, r, a, g)
+        ctx.status_sync()
+        far = np.array([[1e4, 0.0, 0.0], [1e4 + 3.0, 0.0, 0.0]])
+        xb = np.concatenate([m.coords, far])
+        rb = np.concatenate([m.radii, [1.5, 1.5]])
+        ab = torch.empty(n + 2, dtype=torch.float64, device="cuda")
+        gb = torch.empty((n + 2, 3), dtype=torch.float64, device="cuda")
+        ctx.compute_batch(np.array([0, n, n + 2]), _dev(torch, xb), _dev(torch, rb), ab, gb)
+        ctx.status_sync()
+        assert np.array_equal(a.cpu().numpy(), ab.cpu().numpy()[:n]), n
+        assert np.array_equal(g.cpu().numpy(), gb.cpu().numpy()[:n]), n
+    ctx.close()
+
+
 def test_kernel_launch_count(api, torch_cuda, gen):
     """The library's launch counter: one small molecule takes the one-block cell-list build,
     the fused cell + classification kernel, the terms kernel and the (empty) large pass."""
