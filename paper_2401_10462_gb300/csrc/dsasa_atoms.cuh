@@ -30,6 +30,7 @@
 #include "dsasa_kernels.cuh"
 #include "dsasa_math.cuh"
 
+#include <stddef.h>
 #include <stdint.h>
 
 namespace dsasa {
@@ -97,6 +98,10 @@ template <class R, int NE, int NT> struct CellRec {
     int iK, icl;
     int nc, hw, flag, pad;
 };
+using CellRecF = CellRec<float, 64, 64>;
+using CellRecD = CellRec<double, 64, 64>;
+static_assert(offsetof(CellRecF, iK) % 16 == 0 && offsetof(CellRecD, iK) % 16 == 0,
+              "the record header (iK, icl, nc, hw) is read as one 16-byte load");
 
 // one plane row (4 values of R) between the shared table and a cell record, 16-byte moves
 template <class R> __device__ __forceinline__ void copy_row(R* dst, const R* src) {
@@ -105,6 +110,30 @@ template <class R> __device__ __forceinline__ void copy_row(R* dst, const R* src
     } else {
         ((double2*)dst)[0] = ((const double2*)src)[0];
         ((double2*)dst)[1] = ((const double2*)src)[1];
+    }
+}
+
+// a plane row held in registers (16-byte loads and stores)
+template <class R> struct Row4 {
+    R v[4];
+};
+template <class R> __device__ __forceinline__ Row4<R> load_row(const R* src) {
+    Row4<R> r;
+    if constexpr (sizeof(R) == 4) {
+        const float4 f = *(const float4*)src;
+        r.v[0] = f.x; r.v[1] = f.y; r.v[2] = f.z; r.v[3] = f.w;
+    } else {
+        const double2 d0 = ((const double2*)src)[0], d1 = ((const double2*)src)[1];
+        r.v[0] = d0.x; r.v[1] = d0.y; r.v[2] = d1.x; r.v[3] = d1.y;
+    }
+    return r;
+}
+template <class R> __device__ __forceinline__ void store_row(R* dst, const Row4<R>& r) {
+    if constexpr (sizeof(R) == 4) {
+        *(float4*)dst = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    } else {
+        ((double2*)dst)[0] = make_double2(r.v[0], r.v[1]);
+        ((double2*)dst)[1] = make_double2(r.v[2], r.v[3]);
     }
 }
 
@@ -842,27 +871,80 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             if constexpr (PH == PH_CELL) continue;
         }
         } else {
-            // ---------------- the cell built by the cell kernel
-            if (rec->flag != CELL_OK) continue;
-            nc = rec->nc;
-            const int np = NG + nc, hw = rec->hw;
+            // ---------------- the cell built by the cell kernel: the header, then every load of
+            // the record before any shared-memory store (one memory round trip, not one per
+            // table); two plane rows and two vertex slots per lane
+            static_assert(NE <= 64 && NT <= 64, "a record holds at most 64 planes and 64 vertex slots");
+            const int flag = rec->flag;
+            const int4 hd = *reinterpret_cast<const int4*>(&rec->iK);   // iK, icl, nc, hw
+            if (flag != CELL_OK) continue;
+            nc = hd.z;
+            const int np = NG + nc, hw = hd.w;
             nrounds = (hw + 31) >> 5;
-            for (int e = lane; e < np; e += 32) {
-                copy_row(S->pq[e], rec->pq[e]);
-                S->pB[e] = rec->pB[e];
-                S->pg[e] = rec->pg[e];
-                S->start[e] = rec->start[e];
-            }
-            for (int t = lane; t < 32 * nrounds; t += 32) {
-                S->tv[t] = t < hw ? rec->tv[t] : make_uchar4(NONE, NONE, NONE, 0);
-                S->ta[t] = t < hw ? rec->ta[t] : make_uchar4(NONE, NONE, NONE, 0);
-            }
-            if constexpr (PH == PH_TERMS || PH == PH_VOL)
-                for (int e = lane; e < np; e += 32) S->eflag[e] = rec->eflag[e];
-            if constexpr (PH == PH_TERMS) {
+            constexpr bool BATCH_LOADS = PH == PH_CLASS || PH == PH_VOL;
+            if constexpr (BATCH_LOADS) {
+                Row4<R> rq[2];
+                R rb[2];
+                int rg[2];
+                uint8_t rs[2], ref[2] = {0, 0}, rkf[2] = {0, 0}, rtf[2] = {0, 0};
+                uchar4 rtv[2], rta[2];
+    #pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int e = lane + 32 * h;
+                    if (e < np) {
+                        rq[h] = load_row(rec->pq[e]);
+                        rb[h] = rec->pB[e];
+                        rg[h] = rec->pg[e];
+                        rs[h] = rec->start[e];
+                        if constexpr (PH == PH_TERMS || PH == PH_VOL) ref[h] = rec->eflag[e];
+                    }
+                    rtv[h] = rta[h] = make_uchar4(NONE, NONE, NONE, 0);
+                    if (e < hw) {
+                        rtv[h] = rec->tv[e];
+                        rta[h] = rec->ta[e];
+                        if constexpr (PH == PH_TERMS) {
+                            rkf[h] = rec->kf[e];
+                            rtf[h] = rec->tf[e];
+                        }
+                    }
+                }
+    #pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int e = lane + 32 * h;
+                    if (e < np) {
+                        store_row(S->pq[e], rq[h]);
+                        S->pB[e] = rb[h];
+                        S->pg[e] = rg[h];
+                        S->start[e] = rs[h];
+                        if constexpr (PH == PH_TERMS || PH == PH_VOL) S->eflag[e] = ref[h];
+                    }
+                    if (e < 32 * nrounds) {
+                        S->tv[e] = rtv[h];
+                        S->ta[e] = rta[h];
+                        if constexpr (PH == PH_TERMS) {
+                            S->kf[e] = rkf[h];
+                            S->tf[e] = rtf[h];
+                        }
+                    }
+                }
+            } else {
+                for (int e = lane; e < np; e += 32) {
+                    copy_row(S->pq[e], rec->pq[e]);
+                    S->pB[e] = rec->pB[e];
+                    S->pg[e] = rec->pg[e];
+                    S->start[e] = rec->start[e];
+                }
                 for (int t = lane; t < 32 * nrounds; t += 32) {
-                    S->kf[t] = t < hw ? rec->kf[t] : 0;
-                    S->tf[t] = t < hw ? rec->tf[t] : 0;
+                    S->tv[t] = t < hw ? rec->tv[t] : make_uchar4(NONE, NONE, NONE, 0);
+                    S->ta[t] = t < hw ? rec->ta[t] : make_uchar4(NONE, NONE, NONE, 0);
+                }
+                if constexpr (PH == PH_TERMS || PH == PH_VOL)
+                    for (int e = lane; e < np; e += 32) S->eflag[e] = rec->eflag[e];
+                if constexpr (PH == PH_TERMS) {
+                    for (int t = lane; t < 32 * nrounds; t += 32) {
+                        S->kf[t] = t < hw ? rec->kf[t] : 0;
+                        S->tf[t] = t < hw ? rec->tf[t] : 0;
+                    }
                 }
             }
             if (lane == 0) { S->hw = hw; S->bad = 0; }
