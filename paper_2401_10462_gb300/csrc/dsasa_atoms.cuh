@@ -1060,6 +1060,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         const FF Ri_ff = {ri2.x, ri2.y}, Ri2_ff = ff_mul(Ri_ff, Ri_ff);
         FF acc_ff = {0.f, 0.f};
         float cf_sum = 0.f;
+        float vtx_const = 0.f;   // 2 when the vertex term is present: its 4 pi R_i^2 = 2 (2 pi R_i^2)
         const float TWO_PI_H = 6.28318548202514648f, TWO_PI_L = -1.74845553e-07f;   // 2 pi = H + L
         int myEK = 0;
         // edge term of A_i and its gradient gathers, for an edge (i, a) of C that is not closed;
@@ -1087,7 +1088,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 dR2 = (R)((c.Ri - Ra) * (c.Ri + Ra));
             }
             if (GRAD) {
-                const R waf = (R)(A.w ? A.w[ga] : 1.0);
+                const R waf = A.w ? (R)A.w[ga] : (R)1;
                 const R ti = (dr * dr + dR2) * inv2d, ta = (dr * dr - dR2) * inv2d;
                 const R phi = (R)1 - phi_sum * (R)(1.0 / TWO_PI);
                 // vertex + edge parts of the dihedral derivatives around ia (Eq. inexclu)
@@ -1264,8 +1265,14 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 uchar4 v = S->tv[r * 32 + lane];
                 om += solid_angle_half_ol(ppos(S, v.x), ppos(S, v.y), ppos(S, v.z));
             }
-            double omd = warp_sum_d((double)om);
-            if (lane == 0) area_acc += c.Ri * c.Ri * (2.0 * TWO_PI - 2.0 * omd);
+            if constexpr (FFM) {
+                // - 2 R_i^2 (half solid angles) in float-float; the 4 pi R_i^2 is added once below
+                acc_ff = ff_add(acc_ff, ff_mul_f(Ri2_ff, -2.f * om));
+                vtx_const = 2.f;
+            } else {
+                double omd = warp_sum_d((double)om);
+                if (lane == 0) area_acc += c.Ri * c.Ri * (2.0 * TWO_PI - 2.0 * omd);
+            }
         }
 
         // triangle terms: c_iab S_iab^(i) (Eq. trianglev) and the gradient of the triangle
@@ -1326,7 +1333,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 }
                 if (GRAD && part < 3) {
                     const P3<R> O = {zero, zero, zero};
-                    const R waf = (R)(A.w ? A.w[ga] : 1.0), wbf = (R)(A.w ? A.w[gb] : 1.0);
+                    const R waf = A.w ? (R)A.w[ga] : (R)1, wbf = A.w ? (R)A.w[gb] : (R)1;
                     // owner i: d/dp_i = -(g2 + g3); owner a: p_i is the second centre; owner b
                     const P3<R> u = part == 0 ? pa : (part == 1 ? O - pa : O - pb);
                     const P3<R> w = part == 0 ? pb : (part == 1 ? pb - pa : pa - pb);
@@ -1360,10 +1367,13 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
 
         double gxd = 0.0, gyd = 0.0, gzd = 0.0;
         if constexpr (FFM) {
-            area_acc += ff_to_double(acc_ff);
-            area_acc = warp_sum_d(area_acc);
+            // one float-float warp sum of every lane's terms (the same order on every run; lane 0's
+            // value is used), then the per-atom constants (2 + c) 2 pi R_i^2 in FP64
+            FF tot = acc_ff;
+            for (int o = 16; o > 0; o >>= 1)
+                tot = ff_add(tot, FF{__shfl_xor_sync(FULL, tot.h, o), __shfl_xor_sync(FULL, tot.l, o)});
             for (int o = 16; o > 0; o >>= 1) cf_sum += __shfl_xor_sync(FULL, cf_sum, o);
-            area_acc += (double)cf_sum * TWO_PI * c.Ri * c.Ri;
+            area_acc = ff_to_double(tot) + ((double)cf_sum + (double)vtx_const) * TWO_PI * c.Ri * c.Ri;
             if (GRAD) {
                 for (int o = 16; o > 0; o >>= 1) {
                     gx += __shfl_xor_sync(FULL, gx, o);
