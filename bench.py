@@ -119,17 +119,23 @@ def kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the atom kernel from the last ncu capture, only if the kernel
-    sources are the ones that capture measured (else None)."""
+def measured_counters():
+    """Counters of one launch of the dominant kernel from the last ncu capture
+    (profiles/traffic.json), only if the kernel sources are the ones that capture measured
+    (else an empty dict)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
-        return None
+        return {}
     try:
         d = json.load(open(path))
     except Exception:
-        return None
-    return d.get("bytes_per_launch") if d.get("kernel_sha") == kernel_sha() else None
+        return {}
+    return d if d.get("kernel_sha") == kernel_sha() else {}
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the dominant kernel from the last ncu capture (or None)."""
+    return measured_counters().get("bytes_per_launch")
 
 
 def dist_env():
@@ -332,6 +338,16 @@ def run_gpu(args):
     phase_flop = {"cell": FLOP_STAR_TET * STAR_TETS_PER_ATOM * n, "terms": fwd * n}
     dom = max(ph_mixed, key=lambda k: ph_mixed[k])
     dom_ms = ph_mixed[dom]
+    # the kernel is bound by instruction issue: its warp instructions per launch (ncu) over its
+    # live duration, against 152 SMs x 4 schedulers x 1 instruction per cycle at the max clock
+    inst = measured_counters().get("warp_instructions_per_launch")
+    issue_peak = 152 * 4 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
+    issue = None
+    if inst and dom_ms > 0:
+        ach = inst / (dom_ms / 1e3) / 1e9
+        issue = {"warp_inst_per_launch": inst, "achieved_ginst_s": ach, "peak_ginst_s": issue_peak,
+                 "frac": ach / issue_peak,
+                 "source": "smsp__inst_executed.sum of one launch (profiles/traffic.json) / live duration"}
     achieved = phase_flop.get(dom, 0.0) / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else 0.0
     terms_tf = phase_flop["terms"] / (ph_mixed["terms"] / 1e3) / 1e12 if ph_mixed["terms"] > 0 else 0.0
     line = {
@@ -347,7 +363,7 @@ def run_gpu(args):
                      "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
                      "traffic": traffic, "kernel_ms": dom_ms,
                      "peak_source": "FP32 vector peak derived: 152 SMs x 128 lanes x 2 x max SM clock",
-                     "work_model_flop_per_launch": phase_flop.get(dom, 0.0),
+                     "work_model_flop_per_launch": phase_flop.get(dom, 0.0), "issue": issue,
                      "note": "achieved = algorithmic flop of the dominant kernel per launch / its mean "
                              "CUDA-event duration (events between the library's kernels, over K steps of "
                              "the same workload run right after the timed steps)"},

@@ -467,30 +467,52 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 int cx = min(max((int)floorf((fi.x - G.lo[0]) * G.inv_cell), 0), G.dims[0] - 1);
                 int cy = min(max((int)floorf((fi.y - G.lo[1]) * G.inv_cell), 0), G.dims[1] - 1);
                 int cz = min(max((int)floorf((fi.z - G.lo[2]) * G.inv_cell), 0), G.dims[2] - 1);
-                for (int dz = -1; dz <= 1; ++dz) {
-                    int z = cz + dz;
-                    if (z < 0 || z >= G.dims[2]) continue;
-                    for (int dy = -1; dy <= 1; ++dy) {
-                        int y = cy + dy;
-                        if (y < 0 || y >= G.dims[1]) continue;
-                        int row = G.base + (z * G.dims[1] + y) * G.dims[0];
-                        int x0 = max(cx - 1, 0), x1 = min(cx + 1, G.dims[0] - 1);
-                        int beg = A.cstart[row + x0], end = A.cstart[row + x1 + 1];
-                        for (int b0 = beg; b0 < end; b0 += 32) {
-                            int k = b0 + lane;
-                            bool ok = false;
-                            int j = -1;
-                            if (k < end) {
-                                float4 fj = A.sf4[k];
-                                j = A.sidx[k];
-                                float dx = fj.x - fi.x, dy2 = fj.y - fi.y, dz2 = fj.z - fi.z;
-                                float rr = fi.w + fj.w + G.margin;
-                                ok = (j != i) && (dx * dx + dy2 * dy2 + dz2 * dz2 < rr * rr);
-                            }
-                            unsigned bal = __ballot_sync(FULL, ok);
-                            int pos = nc + __popc(bal & lanemask_lt());
-                            if (ok && pos < KMAX) S->pg[NG + pos] = j;
-                            nc += __popc(bal);
+                // sorted positions [beg, end): the atoms that may overlap B_i (FP32 test with the
+                // grid's certified slack) are appended to the candidate table
+                auto gather_range = [&](int beg, int end) {
+                    for (int b0 = beg; b0 < end; b0 += 32) {
+                        int k = b0 + lane;
+                        bool ok = false;
+                        int j = -1;
+                        if (k < end) {
+                            float4 fj = A.sf4[k];
+                            j = A.sidx[k];
+                            float dx = fj.x - fi.x, dy2 = fj.y - fi.y, dz2 = fj.z - fi.z;
+                            float rr = fi.w + fj.w + G.margin;
+                            ok = (j != i) && (dx * dx + dy2 * dy2 + dz2 * dz2 < rr * rr);
+                        }
+                        unsigned bal = __ballot_sync(FULL, ok);
+                        int pos = nc + __popc(bal & lanemask_lt());
+                        if (ok && pos < KMAX) S->pg[NG + pos] = j;
+                        nc += __popc(bal);
+                    }
+                };
+                if constexpr (PH == PH_CELL) {
+                    // the 9 rows (dz, dy) of 3 cells along x: lane r < 9 looks up row r's range, so
+                    // that the 18 lookups are one memory round trip (measured faster in the split
+                    // cell kernel, slower in the one-wave kernel, which keeps the row loop)
+                    int rbeg = 0, rend = 0;
+                    if (lane < 9) {
+                        const int z = cz + lane / 3 - 1, y = cy + lane % 3 - 1;
+                        if (z >= 0 && z < G.dims[2] && y >= 0 && y < G.dims[1]) {
+                            const int row = G.base + (z * G.dims[1] + y) * G.dims[0];
+                            const int x0 = max(cx - 1, 0), x1 = min(cx + 1, G.dims[0] - 1);
+                            rbeg = A.cstart[row + x0];
+                            rend = A.cstart[row + x1 + 1];
+                        }
+                    }
+                    for (int row9 = 0; row9 < 9; ++row9)
+                        gather_range(__shfl_sync(FULL, rbeg, row9), __shfl_sync(FULL, rend, row9));
+                } else {
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        int z = cz + dz;
+                        if (z < 0 || z >= G.dims[2]) continue;
+                        for (int dy = -1; dy <= 1; ++dy) {
+                            int y = cy + dy;
+                            if (y < 0 || y >= G.dims[1]) continue;
+                            int row = G.base + (z * G.dims[1] + y) * G.dims[0];
+                            int x0 = max(cx - 1, 0), x1 = min(cx + 1, G.dims[0] - 1);
+                            gather_range(A.cstart[row + x0], A.cstart[row + x1 + 1]);
                         }
                     }
                 }
