@@ -33,10 +33,10 @@ import numpy as np  # noqa: E402
 
 METRIC = "SASA+grad atoms/s on 1 GB300 vs all-FP64 GPU form; serving p50/p99 latency"
 UNIT = "atoms/s"
-WORKLOAD = {"workload": "globule-5000 (configs[1]): 5,000-atom synthetic globule, seed 0, probe 1.4 A, "
+WORKLOAD = {"workload": "globule-5000: 5,000-atom synthetic globule, seed 0, probe 1.4 A, "
                         "SASA + gradient, FP32 terms / FP64+exact predicates"}
 N_ATOMS, SEED = 5000, 0
-# per-atom algorithmic FP32 work model (flop) of the hot path, see DESIGN.md "Roofline":
+# per-atom algorithmic FP32 work model (flop) of the hot path:
 # 82 per tetrahedron of the atom's star (certification), 145 per boundary tetrahedron term
 # (solid angle + 3 dihedrals), 15 per boundary edge (cap), 180 per boundary triangle; the
 # gradient adds 3x the forward term work.
@@ -434,7 +434,7 @@ def run_reference(args):
 
 
 def serving_measure(count: int, pool: int, loads=(0.8,), seed: int = 0, slots: int = 3):
-    """configs[3]: log-uniform 300-50,000-atom requests (70 % globules, 30 % RNA), Poisson
+    """Serving stream: log-uniform 300-50,000-atom requests (70 % globules, 30 % RNA), Poisson
     arrivals.  The saturated throughput mu is measured first (all requests queued at t = 0);
     then the stream is replayed at lambda = load x mu and p50 / p99 latency (arrival to
     result on the host) are reported."""
@@ -461,7 +461,7 @@ def serving_measure(count: int, pool: int, loads=(0.8,), seed: int = 0, slots: i
 
 
 def run_capsid(args):
-    """configs[4]: the 1,000,000-atom capsid-like shell, mixed vs FP64, SASA + gradient."""
+    """The 1,000,000-atom capsid-like shell, mixed vs FP64, SASA + gradient."""
     import torch
     from paper_2401_10462_gb300 import api, inputs
     m = inputs.make("shell", 1_000_000, 0)
@@ -488,20 +488,20 @@ def run_capsid(args):
         ms = e0.elapsed_time(e1) / steps
         res[prec] = {"ms_per_step": ms, "atoms_per_s": m.n / ms * 1e3, "total_sasa": float(a.sum().item())}
         ctx.close()
-    print(json.dumps({"workload": "capsid shell 1,000,000 atoms (configs[4])", "outer_radius_A": m.extent,
+    print(json.dumps({"workload": "capsid shell 1,000,000 atoms", "outer_radius_A": m.extent,
                       "density_per_A3": m.density(), "inputs_larger_than_L2": True, **res,
                       "mixed_over_fp64": res["mixed"]["atoms_per_s"] / res["fp64"]["atoms_per_s"]}), flush=True)
 
 
 def run_trajectory(args):
-    """configs[2]: 20,000-atom globule, E_np through the autograd Function, Gaussian steps
+    """Trajectory: 20,000-atom globule, E_np through the autograd Function, Gaussian steps
     (sigma 0.01 A) replayed from one captured CUDA graph; reports ms per graphed step without
     and with Verlet-skin lists (skin 1 A: rebuilt on the device once an atom moved 0.5 A)."""
     import torch
     from paper_2401_10462_gb300 import autograd as ag, inputs
     m = inputs.make("globule", 20000, 0)
     dev = torch.device("cuda", 0)
-    out = {"workload": "graphed trajectory, 20,000-atom globule (configs[2])"}
+    out = {"workload": "graphed trajectory, 20,000-atom globule"}
     for skin in (0.0, 1.0):
         tr = ag.GraphedTrajectory(torch.as_tensor(m.coords, device=dev), torch.as_tensor(m.radii, device=dev),
                                   sigma=0.01, seed=0, skin=skin).capture()
@@ -539,7 +539,7 @@ def main():
     elif args.workload == "trajectory":
         run_trajectory(args)
     elif args.workload == "serving":
-        print(json.dumps({"workload": "serving stream (configs[3])",
+        print(json.dumps({"workload": "serving stream, 4,096 requests of 300-50,000 atoms",
                           **serving_measure(4096, 32, loads=(0.5, 0.8, 0.95))}), flush=True)
     else:
         run_gpu(args)

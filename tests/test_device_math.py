@@ -80,7 +80,7 @@ def _random_config(rng, kind, near):
     pts[:, 3] = rng.choice([1.2, 1.52, 1.55, 1.7, 1.8], size=npl + 1) + P
     if near:
         # scale the last radius to bring the predicate near its zero set: bisect on the
-        # FP64 value of the defining quantity with the oracle as the judge
+        # FP64 value of the defining quantity, the oracle's exact sign deciding
         lo, hi = 0.3, 6.0
         for _ in range(60):
             mid = 0.5 * (lo + hi)
