@@ -165,7 +165,9 @@ dsasa_status dsasa_deferred_count(dsasa_ctx* ctx, int64_t* deferred);
  * to *calls_out (may be NULL), and resets the sums.  Phases: */
 #define DSASA_NPHASE 5
 #define DSASA_PHASE_CELL_LIST 0   /* cell-list build (input pass, grid, scan, scatter) */
-#define DSASA_PHASE_CELL 1        /* restricted power cell per atom (gather, sort, clipping) */
+#define DSASA_PHASE_CELL 1        /* restricted power cell per atom (gather, sort, clipping); when
+                                     all atoms fit one wave of the GPU this kernel also classifies,
+                                     and DSASA_PHASE_CLASSIFY is (near) zero */
 #define DSASA_PHASE_CLASSIFY 2    /* simplices of the cell in C (Steps 2a-2c) */
 #define DSASA_PHASE_TERMS 3       /* area terms and gradient gathers */
 #define DSASA_PHASE_LARGE 4       /* the large-capacity pass over deferred atoms */
