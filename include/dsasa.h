@@ -58,8 +58,15 @@ typedef enum {
 
 /* Precision of the arithmetic (the predicates that decide which simplices exist are exact
  * in both modes):
- *   DSASA_MIXED - area/gradient terms in FP32 (sqrt, atan2 in float), FP64 accumulation;
- *                 predicates filtered in FP32, then FP64, then exact expansions.
+ *   DSASA_MIXED - the geometry of every area and gradient term (vectors, triple points,
+ *                 sqrt, atan2) in FP32; the radius quantities (R_i, R_i^2, R_i^2 - R_j^2)
+ *                 enter the area terms as float-float pairs and all area terms of an atom are
+ *                 one float-float warp sum; the per-atom constants (multiples of 2 pi R_i^2)
+ *                 are added once in FP64.  The gradient is summed in FP32.  Predicates are
+ *                 filtered in FP32, then FP64, then decided by exact expansions.
+ *                 Limit: an atom whose exposed area is a sliver (about 1e-5 A^2) gets its
+ *                 gradient from terms that cancel about a million-fold, so its FP32 gradient
+ *                 can miss a 1e-3 relative bound; DSASA_FP64 has no such limit.
  *   DSASA_FP64  - every term in FP64; predicates filtered in FP64, then exact. */
 enum { DSASA_MIXED = 0, DSASA_FP64 = 1 };
 
@@ -179,6 +186,12 @@ dsasa_status dsasa_kernel_times(dsasa_ctx* ctx, double* ms_out, int64_t* calls_o
  * counted).  Diagnostics, no paper counterpart; thread-safe. */
 int64_t dsasa_kernel_launches(void);
 
+/* Test hook for the error path of an exhausted device (no paper counterpart): the next
+ * `count` device allocations that the library attempts fail as if cudaMalloc had returned
+ * cudaErrorMemoryAllocation (nothing is allocated; the call that needed the memory returns
+ * DSASA_ERR_OOM and leaves its context usable).  count <= 0 clears it.  Thread-safe. */
+void dsasa_debug_fail_allocations(int count);
+
 /* Diagnostic export of the dual complex C as seen by each atom's local cell.  For every atom
  * i and every simplex of C that contains i, one record of 5 int32 is written to `records`
  * (device, capacity `max_records`): {i, v0, v1, v2, v3} with the simplex's atom indices in
@@ -202,8 +215,10 @@ dsasa_status dsasa_export_complex(dsasa_ctx* ctx, const double* coords, const do
  *     DSASA_NOALLOC_MAX_ATOMS atoms and reserved on every GPU that loads the library until
  *     the process exits.  n > DSASA_NOALLOC_MAX_ATOMS returns DSASA_ERR_CAPACITY and enqueues
  *     nothing; n = 0 returns DSASA_OK.
- *   - The first call on a device performs a one-time set-up (it looks up the device address
- *     of that array); make this first call before any stream capture begins.
+ *   - Every call looks up the device address of that array in the CUDA context current on
+ *     the calling thread (the address belongs to the context, not to the device ordinal).
+ *     The first call in a context also loads the library's device code there; make that
+ *     first call before any stream capture begins.
  *   - Every call shares the one array, which keeps the previous call's contents: calls that
  *     overlap on the GPU (other streams, other host threads) race.  Serialise them.
  *   - Blocking: the call synchronises `cuda_stream` and returns the device status of this

@@ -184,11 +184,13 @@ def predicate(kind: int, pts_xyzR, ids) -> int:
 
 
 def local_patch(coords, radii, centre_ids, probe: float = PROBE, cutoff: float = None):
-    """Indices of the atoms within `cutoff` of any centre atom.
+    """Indices of the atoms within `cutoff` of any centre atom (sorted).
 
-    A_i and the gradient entry of atom i depend only on atoms whose balls overlap B_i
-    (the Laguerre-intersection cell of i is cut only by them), so a patch of radius
-    2 (R_i + R_max) around i reproduces atom i's outputs exactly."""
+    A_i and the gradient entry g_i of atom i depend only on the atoms whose balls overlap
+    B_i: every simplex of the dual complex that contains i lies in B_i, where a ball that
+    misses B_i never has the smaller power.  A patch of radius R_i + R_max around i therefore
+    reproduces atom i's outputs exactly; the default 4 R_max + 1 A keeps a margin.  Pinned
+    against the whole-molecule oracle in tests/test_oracle_local_patch.py."""
     coords = np.asarray(coords)
     rmax = float(np.max(radii)) + probe
     if cutoff is None:

@@ -54,6 +54,7 @@ _lib.dsasa_set_timing.argtypes = [_vp, ctypes.c_int]
 _lib.dsasa_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_export_complex.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_last_error.argtypes = [_vp]
+_lib.dsasa_debug_fail_allocations.argtypes = [ctypes.c_int]
 _lib.dsasa_kernel_launches.argtypes = []
 _lib.dsasa_kernel_launches.restype = ctypes.c_int64
 _lib.dsasa_last_error.restype = ctypes.c_char_p
@@ -69,7 +70,8 @@ EXPORTED = ("dsasa_default_config", "dsasa_create", "dsasa_set_stream", "dsasa_s
             "dsasa_compute_vjp", "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync",
             "dsasa_export_complex", "dsasa_last_error", "dsasa_destroy", "dsasa_version", "dsasa_deferred_count",
             "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume",
-            "dsasa_compute_sr", "dsasa_sr_tests", "dsasa_lists_reused", "dsasa_kernel_launches")
+            "dsasa_compute_sr", "dsasa_sr_tests", "dsasa_lists_reused", "dsasa_kernel_launches",
+            "dsasa_debug_fail_allocations")
 
 
 class DSASAError(RuntimeError):

@@ -463,6 +463,11 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 nc += __popc(bal);
             }
         } else {
+            // with Verlet lists (skin > 0) the gather also finds the atoms of the skin band:
+            // they go to the atom's list in global memory (nl entries), while the plane table
+            // keeps only the balls that overlap B_i now (the float64 test of the reuse path)
+            const bool store_lists = A.nbl != nullptr;
+            int nl = 0;
             {
                 int cx = min(max((int)floorf((fi.x - G.lo[0]) * G.inv_cell), 0), G.dims[0] - 1);
                 int cy = min(max((int)floorf((fi.y - G.lo[1]) * G.inv_cell), 0), G.dims[1] - 1);
@@ -480,6 +485,18 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                             float dx = fj.x - fi.x, dy2 = fj.y - fi.y, dz2 = fj.z - fi.z;
                             float rr = fi.w + fj.w + G.margin;
                             ok = (j != i) && (dx * dx + dy2 * dy2 + dz2 * dz2 < rr * rr);
+                        }
+                        if (store_lists) {
+                            const unsigned bl = __ballot_sync(FULL, ok);
+                            const int lp = nl + __popc(bl & lanemask_lt());
+                            if (ok && lp < NBL_CAP) A.nbl[(size_t)i * NBL_CAP + lp] = j;
+                            nl += __popc(bl);
+                            if (ok) {
+                                const double ddx = A.xyz[3 * j] - c.pi[0], ddy = A.xyz[3 * j + 1] - c.pi[1],
+                                             ddz = A.xyz[3 * j + 2] - c.pi[2];
+                                const double rr64 = c.Ri + A.R[j];
+                                ok = ddx * ddx + ddy * ddy + ddz * ddz < rr64 * rr64 * (1.0 + 1e-9);
+                            }
                         }
                         unsigned bal = __ballot_sync(FULL, ok);
                         int pos = nc + __popc(bal & lanemask_lt());
@@ -517,20 +534,14 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                     }
                 }
             }
-            if (A.nbl) {
-                // store the list and the reference position for the next calls (a deferred
-                // atom's list is stored by the large-capacity pass, which gathers all of it)
-                __syncwarp();
-                if (nc <= KMAX) {
-                    for (int k = lane; k < nc; k += 32) A.nbl[(size_t)i * NBL_CAP + k] = S->pg[NG + k];
-                    if (lane == 0) A.nbn[i] = nc;
-                } else if (!can_defer && lane == 0) {
-                    atomicOr(A.lists_bad, 1);
-                }
-                if (lane == 0) {
-                    for (int k = 0; k < 3; ++k) A.ref_xyz[3 * i + k] = A.xyz[3 * i + k];
-                    A.ref_rad[i] = A.radii_in[i];
-                }
+            if (store_lists && lane == 0) {
+                // the list's length and the reference position for the next calls; a list
+                // longer than its capacity makes the next call rebuild (a deferred atom writes
+                // the same list again in the large-capacity pass)
+                if (nl <= NBL_CAP) A.nbn[i] = nl;
+                else atomicOr(A.lists_bad, 1);
+                for (int k = 0; k < 3; ++k) A.ref_xyz[3 * i + k] = A.xyz[3 * i + k];
+                A.ref_rad[i] = A.radii_in[i];
             }
         }
         if (nc > KMAX && can_defer) {

@@ -20,6 +20,20 @@ constexpr int kTimingRing = 256;
 
 namespace {
 std::atomic<long long> g_launches{0};   // kernels launched by this library (all contexts)
+std::atomic<int> g_fail_allocs{0};      // dsasa_debug_fail_allocations: allocations left to fail
+
+// every device allocation of the library goes through here (so that the error path of an
+// exhausted device can be tested without exhausting a device)
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    int left = g_fail_allocs.load();
+    while (left > 0) {
+        if (g_fail_allocs.compare_exchange_weak(left, left - 1)) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
 }
 void dsasa::note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
@@ -131,7 +145,7 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
     if (c->cfg.max_cells > 0 && c->cfg.max_cells < nc) nc = std::max<int64_t>(c->cfg.max_cells, 64);
     int64_t nbs = (int64_t)scan_scratch_ints((int)nc) + 16;
 #define ALLOC(ptr, count)                                                               \
-    e = cudaMalloc((void**)&c->ptr, sizeof(*c->ptr) * (size_t)(count));                 \
+    e = dev_alloc((void**)&c->ptr, sizeof(*c->ptr) * (size_t)(count));                 \
     if (e != cudaSuccess) { free_scratch(c); return cuda_fail(c, e, "cudaMalloc " #ptr); }
     ALLOC(R, na) ALLOC(Rhl, na) ALLOC(f4, na) ALLOC(molid, na) ALLOC(rank, na) ALLOC(cell, na) ALLOC(sidx, na) ALLOC(sf4, na)
     ALLOC(bbox, 8 * nm) ALLOC(grids, nm) ALLOC(counts, nc + 1) ALLOC(cstart, nc + 1) ALLOC(blocksums, nbs)
@@ -271,9 +285,9 @@ dsasa_status dsasa_create(dsasa_ctx** out, int device, void* cuda_stream, const 
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaSetDevice(device);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->status, 4 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->nrec, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->sr_tests, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_alloc((void**)&c->status, 4 * sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc((void**)&c->nrec, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_alloc((void**)&c->sr_tests, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -413,7 +427,7 @@ dsasa_status dsasa_compute_host(dsasa_ctx* c, const double* coords_host, const d
         free_host_staging(c);
         int64_t cap = n + n / 4 + 256;
 #define ALLOC(ptr, count)                                                           \
-    e = cudaMalloc((void**)&c->ptr, sizeof(double) * (size_t)(count));             \
+    e = dev_alloc((void**)&c->ptr, sizeof(double) * (size_t)(count));             \
     if (e != cudaSuccess) { free_host_staging(c); return cuda_fail(c, e, "cudaMalloc " #ptr); }
         ALLOC(h_xyz, 3 * cap) ALLOC(h_rad, cap) ALLOC(h_w, cap) ALLOC(h_area, cap) ALLOC(h_grad, 3 * cap)
 #undef ALLOC
@@ -474,7 +488,7 @@ dsasa_status dsasa_export_complex(dsasa_ctx* c, const double* coords, const doub
     dsasa_status st = check_common(c, coords, radii, probe, n, coords);
     if (st != DSASA_OK || n == 0) return st;
     double* areas = nullptr;
-    cudaError_t e = cudaMalloc((void**)&areas, sizeof(double) * (size_t)n);
+    cudaError_t e = dev_alloc((void**)&areas, sizeof(double) * (size_t)n);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc export areas");
     e = cudaMemsetAsync(c->nrec, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) { cudaFree(areas); return cuda_fail(c, e, "memset"); }
@@ -496,6 +510,8 @@ dsasa_status dsasa_export_complex(dsasa_ctx* c, const double* coords, const doub
 const char* dsasa_last_error(const dsasa_ctx* c) { return c ? c->err : "null context"; }
 
 int64_t dsasa_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void dsasa_debug_fail_allocations(int count) { g_fail_allocs.store(count > 0 ? count : 0); }
 
 dsasa_status dsasa_set_timing(dsasa_ctx* c, int enable) {
     if (!c) return DSASA_ERR_ARG;

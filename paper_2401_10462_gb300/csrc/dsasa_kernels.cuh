@@ -127,8 +127,9 @@ struct AtomArgs {
     // Verlet neighbour lists (single molecule, skin > 0; NULL = none): candidates of atom i
     // at nbl[i * NBL_CAP .. + nbn[i]).  *reuse != 0: take the candidates from the lists (the
     // cell list was not rebuilt); else gather them from the cell list and store them with
-    // the reference coordinates and radii.  *lists_bad is set when a list cannot hold its
-    // atom's candidates (the next call rebuilds).
+    // the reference coordinates and radii.  Either way only the balls that overlap B_i at
+    // the current positions enter the plane table.  *lists_bad is set when a list cannot
+    // hold its atom's candidates (the next call rebuilds).
     int* nbl;
     int* nbn;
     const int* reuse;
@@ -137,7 +138,7 @@ struct AtomArgs {
     double* ref_rad;
     const double* radii_in;
 };
-constexpr int NBL_CAP = 122;   // list capacity per atom (the large-capacity pass's)
+constexpr int NBL_CAP = 122;   // list capacity per atom (atoms within R_i + R_j + skin)
 
 // Shrake-Rupley numerical SASA (cross-check): m unit vectors pts[3m] (device)
 struct SRArgs {

@@ -14,8 +14,6 @@
 
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 using namespace dsasa;
 
 namespace {
@@ -45,11 +43,6 @@ constexpr size_t kScratchBytes = al(OFF_SYNC + sizeof(unsigned) * BUILD_SYNC_WOR
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// device address of the array, per device ordinal (the name is only a host-side stand-in)
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char* g_base[kMaxDevices] = {nullptr};
-
 }  // namespace
 
 extern "C" dsasa_status dsasa_compute_noalloc(const double* coords, const double* radii, double probe, int64_t n,
@@ -60,18 +53,17 @@ extern "C" dsasa_status dsasa_compute_noalloc(const double* coords, const double
     if (n > kMaxAtoms) return DSASA_ERR_CAPACITY;   // more atoms than the static scratch holds
     if ((long long)scan_scratch_ints((int)kMaxCells) > 4096) return DSASA_ERR_CAPACITY;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DSASA_ERR_CUDA;
-    unsigned char* base;
+    // The host-side name of the array is only a stand-in; its device address belongs to the
+    // CUDA context that is current now (it changes after a device reset or under another
+    // driver context), so it is looked up on every call, with that context current.  The
+    // lookup is host work only; on the first call in a context it also loads the module,
+    // which is why the first call must come before any stream capture.
+    unsigned char* base = nullptr;
     {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_base[dev]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p) return DSASA_ERR_CUDA;
-            g_base[dev] = (unsigned char*)p;
-        }
-        base = g_base[dev];
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return DSASA_ERR_CUDA;
+        base = (unsigned char*)p;
     }
     int* status = (int*)(base + OFF_STATUS);
     // the array keeps the previous call's contents: clear what must start at zero (the

@@ -11,7 +11,9 @@ device-to-host copies of areas and gradients.  Requests that arrive while other 
 are on the GPU go into the next free slot, so their work overlaps on the device with the
 batches already running.  Latency is measured per request from its arrival to its result
 being on the host.  Results do not depend on the batch composition: every atom's outputs
-are computed from its own molecule only, in a fixed order.
+are computed from its own molecule only, in a fixed order.  Each finished batch's device
+status is read at once and attached to its requests (a failed batch is re-run one request
+at a time, so that the status names the request that caused it).
 """
 from __future__ import annotations
 
@@ -33,6 +35,7 @@ class Request:
     done: float = None
     areas: np.ndarray = None
     grad: np.ndarray = None
+    status: int = None     # the library's status code for this request (0 = OK)
 
     @property
     def n(self):
@@ -100,7 +103,9 @@ class Server:
         slot.batch = batch
         slot.offsets = off
 
-    def _finish(self, slot: _Slot, t_now: float):
+    def _finish(self, slot: _Slot, t0: float):
+        # the slot's stream is idle: reading its device status word costs no wait
+        code = slot.ctx.status_code()
         off = slot.offsets
         ha = slot.h_area.numpy()
         hg = slot.h_grad.numpy()
@@ -108,6 +113,20 @@ class Server:
             r.areas = ha[off[k]:off[k + 1]].copy()
             if self.with_grad:
                 r.grad = hg[off[k]:off[k + 1]].copy()
+            r.status = code
+        if code != api.DSASA_OK and len(slot.batch) > 1:
+            # the status word covers the whole batch: run its requests one by one to find
+            # which of them failed (the others keep the outputs computed just now, which
+            # do not depend on the batch)
+            for r in slot.batch:
+                self._launch(slot, [r])
+                slot.event.synchronize()
+                r.status = slot.ctx.status_code()
+                r.areas = slot.h_area.numpy()[: r.n].copy()
+                if self.with_grad:
+                    r.grad = slot.h_grad.numpy()[: r.n].copy()
+        t_now = time.perf_counter() - t0
+        for r in slot.batch:
             r.done = t_now
         slot.batch = []
         slot.event = None
@@ -129,7 +148,7 @@ class Server:
             progressed = False
             for slot in self.slots:
                 if slot.event is not None and slot.event.query():
-                    self._finish(slot, time.perf_counter() - t0)
+                    self._finish(slot, t0)
                     progressed = True
             done = sum(1 for r in reqs if r.done is not None)
             for slot in self.slots:
@@ -144,12 +163,11 @@ class Server:
                         progressed = True
             if not progressed:
                 time.sleep(50e-6)
-        for slot in self.slots:
-            slot.ctx.status_sync()
         wall = time.perf_counter() - t0
         lat = np.array([r.done - (r.arrival if realtime else 0.0) for r in reqs])
         atoms = sum(r.n for r in reqs)
-        return {"requests": len(reqs), "atoms": atoms, "wall_s": wall, "atoms_per_s": atoms / wall,
+        failed = sum(1 for r in reqs if r.status != api.DSASA_OK)
+        return {"requests": len(reqs), "failed": failed, "atoms": atoms, "wall_s": wall, "atoms_per_s": atoms / wall,
                 "requests_per_s": len(reqs) / wall, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_ms": 1e3 * float(lat.mean())}
 

@@ -92,3 +92,23 @@ def test_serving_results_same_alone_and_in_the_mix(torch_cuda, gen):
         srv1.close()
         assert np.array_equal(alone.areas, q.areas) and np.array_equal(alone.grad, q.grad)
     srv.close()
+
+
+def test_serving_reports_the_failing_request(torch_cuda, gen):
+    """A request with a non-finite coordinate in a batch of six: it alone gets the input
+    error status (its outputs are meaningless), the others their normal results."""
+    from paper_2401_10462_gb300 import serve
+    reqs, _ = serve.request_pool(6, seed=4, pool=3, lo=300, hi=2000)
+    bad = reqs[2]
+    bad.coords = bad.coords.copy()
+    bad.coords[5, 1] = np.nan
+    srv = serve.Server(slots=1, slot_atoms=20000)
+    st = srv.run(reqs, realtime=False)
+    assert st["failed"] == 1 and bad.status == 8
+    for r_ in reqs:
+        if r_ is not bad:
+            assert r_.status == 0 and np.all(np.isfinite(r_.areas)) and np.all(np.isfinite(r_.grad))
+            alone = serve.Request(r_.rid, r_.coords, r_.radii)
+            srv.run([alone], realtime=False)
+            assert np.array_equal(alone.areas, r_.areas)
+    srv.close()

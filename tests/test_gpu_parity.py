@@ -94,20 +94,60 @@ def _complex_sets(rec):
     return out, owners
 
 
-@pytest.mark.parametrize("seed", [0, 5])
-def test_dual_complex_bit_exact(api, torch_cuda, orc, gen, seed):
-    m = gen.globule(304, seed)
-    ctx = api.Context()
-    rec = ctx.export_complex(_dev(torch_cuda, m.coords), _dev(torch_cuda, m.radii)).cpu().numpy()
+def _large_ball_in_shell(m=40, zcut=-2.0):
+    """A large ball inside a partly open shell of small ones: its cell has more vertices than
+    the fast pass holds, so it goes through the large-capacity (128 / 128) pass."""
+    rng = np.random.default_rng(3)
+    idx = np.arange(m) + 0.5
+    z = 1 - 2 * idx / m
+    rr = np.sqrt(1 - z * z)
+    ang = math.pi * (1 + 5 ** 0.5) * idx
+    shell = 5.2 * np.stack([rr * np.cos(ang), rr * np.sin(ang), z], 1) + 1e-5 * rng.normal(size=(m, 3))
+    shell = shell[z > zcut]
+    xyz = np.concatenate([np.zeros((1, 3)) + 1e-6, shell])
+    r = np.concatenate([[3.6], np.full(len(shell), 1.2)])
+    return xyz, r
+
+
+def _check_complex(api, torch, orc, coords, radii, precision):
+    ctx = api.Context(precision=precision)
+    rec = ctx.export_complex(_dev(torch, coords), _dev(torch, radii)).cpu().numpy()
     ctx.status_sync()
+    ctx.close()
     got, owners = _complex_sets(rec)
-    o = orc.Oracle(m.coords, m.radii)
+    o = orc.Oracle(coords, radii)
     for d in range(4):
         ref = {tuple(int(v) for v in np.atleast_1d(s)) for s in o.simplices(d)}
         assert got[d] == ref, (d, len(got[d]), len(ref), list(got[d] ^ ref)[:5])
     # every atom of a simplex sees it in its own cell (consistency of the local cells)
     for simp, who in owners.items():
         assert who == set(simp), (simp, who)
+
+
+COMPLEX_CASES = ["globule304-0", "globule304-5", "globule5000-0", "globule5000-1", "globule5000-2",
+                 "globule7000-12", "rna1000-1", "shell3000-2", "large-ball"]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("case", COMPLEX_CASES)
+def test_dual_complex_bit_exact(api, torch_cuda, orc, gen, case, precision):
+    """The simplices of C that the GPU cells find are exactly the oracle's, on the 304- and
+    5,000-atom globules, a 7,000-atom globule (more atoms than one wave of the cell kernel:
+    separate cell and classification kernels), an RNA, a shell, and a cell that needs the
+    large-capacity pass."""
+    kind, _, seed = case.partition("-")
+    if kind == "large":
+        xyz, r = _large_ball_in_shell()
+    elif kind.startswith("globule"):
+        m = gen.globule(int(kind[7:]), int(seed))
+        xyz, r = m.coords, m.radii
+    elif kind.startswith("rna"):
+        m = gen.rna(int(kind[3:]), int(seed))
+        xyz, r = m.coords, m.radii
+    else:
+        m = gen.shell(int(kind[5:]), int(seed), r_out=45.0, thickness=14.0, chain=100)
+        xyz, r = m.coords, m.radii
+    _check_complex(api, torch_cuda, orc, xyz, r, precision)
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])

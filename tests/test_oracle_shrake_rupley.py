@@ -1,5 +1,6 @@
-"""Pins of the Shrake-Rupley oracle (numerical SASA): exact special cases and convergence to
-the exact (inclusion-exclusion) areas as the point count grows."""
+"""Pins of the Shrake-Rupley oracle (numerical SASA): exact special cases, every decision
+against rational arithmetic on small inputs, an exact tie, and convergence to the exact
+(inclusion-exclusion) areas as the point count grows."""
 import math
 
 import numpy as np
@@ -50,3 +51,36 @@ def test_globule_converges_to_the_exact_areas(orc, gen):
     e2 = np.abs(sr.areas(m.coords, m.radii, 3840) - ex).mean()
     assert e2 < 0.35 * e1
     assert abs(sr.areas(m.coords, m.radii, 3840).sum() - ex.sum()) < 2e-3 * ex.sum()
+
+
+def _brute_exposed(coords, radii, pts, i, probe):
+    """Every point of atom i decided in rational arithmetic against every other ball."""
+    out = []
+    for s in pts:
+        ok = True
+        for j in range(len(radii)):
+            if j != i and sr._exact_margin_sign(coords[i], coords[j], radii[i], radii[j], s, probe) <= 0:
+                ok = False
+                break
+        out.append(ok)
+    return np.array(out)
+
+
+def test_every_decision_matches_rational_arithmetic(gen):
+    m = gen.globule(12, 4)
+    pts = sr.sphere_points(64)
+    for i in range(m.n):
+        assert np.array_equal(sr.exposed_mask(m.coords, m.radii, pts, i), _brute_exposed(m.coords, m.radii, pts, i, P))
+
+
+def test_exact_tie_is_covered_and_near_ties_are_exact():
+    # probe 0 so that R = r exactly.  The point (0, 0, 2) of the sphere of radius 2 at the
+    # origin lies on the sphere of radius 1 centred at (0, 0, 3): not strictly outside.
+    pts = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0]], dtype=np.float32)
+    xyz = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 3.0]])
+    mask = sr.exposed_mask(xyz, np.array([2.0, 1.0]), pts, 0, probe=0.0)
+    assert not mask[0] and mask[1]
+    # near-ties: the ball moved by one ulp of its centre either way
+    for z, exposed in ((np.nextafter(3.0, 4.0), True), (np.nextafter(3.0, 2.0), False)):
+        xyz[1, 2] = z
+        assert sr.exposed_mask(xyz, np.array([2.0, 1.0]), pts, 0, probe=0.0)[0] == exposed
