@@ -1,6 +1,6 @@
 """Benchmark: exact SASA + gradient throughput (atoms/s) on GB300.
 
-Default workload (N = 1): the 5,000-atom synthetic globule (seed 0, probe 1.4 A), per-atom
+Headline workload (N = 1): the 5,000-atom synthetic globule (seed 0, probe 1.4 A), per-atom
 SASA and the gradient of sum_i A_i, FP32 area arithmetic with FP32/FP64/exact predicates
 (the mixed form), next to the all-FP64 GPU form of the same kernels.  One step = one full
 pass of the hot path (cell list, per-atom cells, classification, areas, gradient).
@@ -11,15 +11,23 @@ inputs are smaller than L2.  Multi-GPU runs are independent replicas (the method
 exchange step for independent molecules): every rank processes its own copy, barrier and
 max over ranks, value = atoms of all ranks / slowest rank's time.
 
---impl reference times the CPU oracle (single-threaded, exact predicates) on the same
-workload: the baseline the GPU path is compared against.
+The same JSON line also carries (rank 0, one GPU): the arithmetic roofs measured in this run
+(libdsasa_peaks.so), the roofline of the dominant kernel from the oracle-counted work model
+(profiles/work_model_globule5000.json), the accuracy against the FP64 oracle, the
+1,000,000-atom capsid shell, the graphed 20,000-atom trajectory, the 4,096-request serving
+stream at three loads, each with its own clock record, and the oracle timed on the host.
+
+--impl reference times the CPU oracle (exact predicates, FP64) on the same workload: every
+step is one full pass over the 5,000-atom globule.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -36,28 +44,37 @@ UNIT = "atoms/s"
 WORKLOAD = {"workload": "globule-5000: 5,000-atom synthetic globule, seed 0, probe 1.4 A, "
                         "SASA + gradient, FP32 terms / FP64+exact predicates"}
 N_ATOMS, SEED = 5000, 0
-# per-atom algorithmic FP32 work model (flop) of the hot path:
-# 82 per tetrahedron of the atom's star (certification), 145 per boundary tetrahedron term
-# (solid angle + 3 dihedrals), 15 per boundary edge (cap), 180 per boundary triangle; the
-# gradient adds 3x the forward term work.
-FLOP_STAR_TET, FLOP_TET, FLOP_EDGE, FLOP_TRI, GRAD_FACTOR = 82.0, 145.0, 15.0, 180.0, 4.0
-STAR_TETS_PER_ATOM = 26.0
+WORK_MODEL = os.path.join(ROOT, "profiles", "work_model_globule5000.json")
 
 
-def peaks():
+def driver_peaks():
     p = {"hbm_gbs": 6800.0, "source": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         d = json.load(open(path))
         p.update(d)
         p["source"] = "measured"
-    # FP32 vector peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock
-    p["fp32_tflops"] = 152 * 128 * 2 * float(p.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     return p
 
 
+def measure_peaks(device: int):
+    """FP32 FMA, FP64 FMA, rsqrt and atan2f throughput and the warp-instruction issue rate,
+    measured now on this GPU by libdsasa_peaks.so (CUDA events; no setting is changed)."""
+    from paper_2401_10462_gb300 import build
+    lib = ctypes.CDLL(build.PEAKS_LIB)
+    lib.dsasa_peaks_measure.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    out = (ctypes.c_double * 6)()
+    rc = lib.dsasa_peaks_measure(device, out)
+    if rc != 0:
+        raise RuntimeError(f"peak microbenchmarks failed (CUDA error {rc})")
+    return {"fp32_tflops": out[0], "fp64_tflops": out[1], "rsqrt_gops": out[2], "atan2f_gops": out[3],
+            "issue_ginst_s": out[4], "sms": int(out[5]),
+            "source": "microbenchmarks in this run (libdsasa_peaks.so: FMA / rsqrt / atan2f streams, "
+                      "8 blocks of 256 threads per SM, best of 5, CUDA events)"}
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    """nvidia-smi samples of SM clock and throttle reasons while a measured region runs."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -71,10 +88,11 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
+            time.sleep(0.15)   # the first sample lands inside the region
         except Exception:
             self.proc = None
         return self
@@ -85,6 +103,7 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc:
+            time.sleep(0.06)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -119,11 +138,10 @@ def kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_counters():
+def measured_counters(name="traffic.json"):
     """Counters of one launch of the dominant kernel from the last ncu capture
-    (profiles/traffic.json), only if the kernel sources are the ones that capture measured
-    (else an empty dict)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    (profiles/<name>), only if the kernel sources are the ones that capture measured."""
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return {}
     try:
@@ -133,27 +151,11 @@ def measured_counters():
     return d if d.get("kernel_sha") == kernel_sha() else {}
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the dominant kernel from the last ncu capture (or None)."""
-    return measured_counters().get("bytes_per_launch")
-
-
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
-
-
-def algorithmic_flops_per_atom(rec, n):
-    """Work model applied to the complex the GPU path itself exported (records of C)."""
-    simp = rec[:, 1:]
-    dim = (simp >= 0).sum(1) - 1
-    tets = (dim == 3).sum() / n      # incidences (atom, tetrahedron of C) per atom
-    edges = (dim == 1).sum() / n
-    tris = (dim == 2).sum() / n
-    fwd = FLOP_TET * tets + FLOP_EDGE * edges + FLOP_TRI * tris
-    return FLOP_STAR_TET * STAR_TETS_PER_ATOM + GRAD_FACTOR * fwd, {"tets": tets, "edges": edges, "tris": tris}
 
 
 def replica_throughput(total_s: float, ws: int, n: int, steps: int, device=None) -> float:
@@ -165,6 +167,121 @@ def replica_throughput(total_s: float, ws: int, n: int, steps: int, device=None)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_s = float(t.item())
     return ws * n * steps / total_s
+
+
+class Timer:
+    """K steps of ctx.compute on one molecule, each bracketed by CUDA events, L2 flushed
+    before every timed step; per-kernel phases on K further steps."""
+
+    def __init__(self, api, torch, dev, local, stream, flush):
+        self.api, self.torch, self.dev, self.local, self.stream, self.flush = api, torch, dev, local, stream, flush
+
+    def steps(self, xyz, rad, precision, steps, warmup, grad=True):
+        api, torch = self.api, self.torch
+        n = xyz.shape[0]
+        ctx = api.Context(device=self.local, stream=self.stream, precision=precision)
+        a = torch.empty(n, dtype=torch.float64, device=self.dev)
+        g = torch.empty((n, 3), dtype=torch.float64, device=self.dev) if grad else None
+        with torch.cuda.stream(self.stream):
+            for _ in range(warmup):
+                ctx.compute(xyz, rad, a, g)
+            ctx.status_sync()
+            evs = []
+            k0 = api.kernel_launches()
+            for _ in range(steps):
+                self.flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+                ctx.compute(xyz, rad, a, g)
+                e1.record(self.stream)
+                evs.append((e0, e1))
+            ctx.status_sync()
+        torch.cuda.synchronize(self.dev)
+        launches = api.kernel_launches() - k0
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        ctx.close()
+        return ms, a, g, launches
+
+    def phases(self, xyz, rad, precision, steps, grad=True):
+        """Mean device time per kernel phase: the same steps with CUDA events recorded between
+        the library's kernels (the events hold back the early launch of each next kernel, so
+        these steps are not the timed ones)."""
+        api, torch = self.api, self.torch
+        n = xyz.shape[0]
+        ctx = api.Context(device=self.local, stream=self.stream, precision=precision)
+        a = torch.empty(n, dtype=torch.float64, device=self.dev)
+        g = torch.empty((n, 3), dtype=torch.float64, device=self.dev) if grad else None
+        with torch.cuda.stream(self.stream):
+            ctx.compute(xyz, rad, a, g)
+            ctx.status_sync()
+            ctx.set_timing(True)
+            for _ in range(steps):
+                self.flush.zero_()
+                ctx.compute(xyz, rad, a, g)
+            ctx.status_sync()
+        torch.cuda.synchronize(self.dev)
+        ph, calls = ctx.kernel_times()
+        ctx.close()
+        return {k: v / max(calls, 1) for k, v in ph.items()}
+
+
+def roofline_block(wm, n, ph, pk, dpk, counters):
+    """The dominant kernel's roofline from the oracle-counted work model (per-atom flop x the
+    atoms one launch processes / its mean CUDA-event duration) against the roofs measured in
+    this run, plus the terms kernel and the instruction-issue roof."""
+    dom = max(ph, key=lambda k: ph[k])
+    flop = {"cell": wm["cell_flop_per_atom"] * n, "terms": wm["terms_flop_per_atom"] * n}
+    dom_ms = ph[dom]
+    achieved = flop.get(dom, 0.0) / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else 0.0
+    issue = None
+    inst = counters.get("warp_instructions_per_launch")
+    if inst and dom_ms > 0:
+        ach = inst / (dom_ms / 1e3) / 1e9
+        issue = {"warp_inst_per_launch": inst, "achieved_ginst_s": ach, "peak_ginst_s": pk["issue_ginst_s"],
+                 "frac": ach / pk["issue_ginst_s"],
+                 "source": "smsp__inst_executed.sum of one ncu launch (profiles/traffic.json) / live duration; "
+                           "peak = warp instructions/s of the FP32 FMA microbenchmark"}
+    names = {"cell": "k_atoms<float,0,64,64,PH_CC or PH_CELL> (restricted power cell; with all atoms in one wave "
+                     "also the classification)", "terms": "k_atoms<float,1,64,64,PH_TERMS>"}
+    out = {"bound": "alu", "kernel": names.get(dom, dom), "achieved": achieved, "peak": pk["fp32_tflops"],
+           "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"], "traffic": counters.get("bytes_per_launch"),
+           "kernel_ms": dom_ms, "peak_source": "FP32 FMA roof measured in this run (of measured)",
+           "frac_of_fp64_roof": achieved / pk["fp64_tflops"],
+           "work_model": f"{wm['flop_table']['certification']:.0f} flop per star tetrahedron x "
+                         f"{wm['star_tets_per_atom']:.2f} per atom (oracle counts, profiles/work_model_globule5000.json)",
+           "work_model_flop_per_launch": flop.get(dom, 0.0), "issue": issue,
+           "hbm_peak_gbs": dpk.get("hbm_gbs"), "hbm_peak_source": dpk.get("source"),
+           "note": "achieved = algorithmic flop per launch / mean CUDA-event duration of the kernel (events "
+                   "between the library's kernels, K steps of the same workload after the timed steps)"}
+    t_ms = ph.get("terms", 0.0)
+    terms = None
+    if t_ms > 0:
+        tf = flop["terms"] / (t_ms / 1e3) / 1e12
+        sfu = wm["terms_sfu_per_atom"] * n / (t_ms / 1e3) / 1e9
+        terms = {"kernel_ms": t_ms, "achieved_tflops": tf, "frac_of_fp32_roof": tf / pk["fp32_tflops"],
+                 "achieved_sfu_gops": sfu, "frac_of_rsqrt_roof": sfu / pk["rsqrt_gops"],
+                 "work_model_flop_per_launch": flop["terms"]}
+    return out, terms
+
+
+def accuracy(ra, rg, a, g):
+    """Errors of one GPU result against the FP64 oracle: plain relative and with the floors
+    of the stated tolerances (areas max(A, 1 A^2), gradients max(|g|, 1e-2))."""
+    a, g = np.asarray(a), np.asarray(g)
+    da = np.abs(a - ra)
+    dg = np.linalg.norm(g - rg, axis=1)
+    gn = np.linalg.norm(rg, axis=1)
+    pos, gpos = ra > 0, gn > 0
+    return {"max_area_rel": float((da[pos] / ra[pos]).max()) if pos.any() else 0.0,
+            "max_area_rel_floor1": float((da / np.maximum(ra, 1.0)).max()),
+            "total_rel": float(abs(a.sum() - ra.sum()) / ra.sum()),
+            "max_grad_rel": float((dg[gpos] / gn[gpos]).max()) if gpos.any() else 0.0,
+            "max_grad_rel_floor": float((dg / np.maximum(gn, 1e-2)).max()),
+            "n_area_over_1e-4_rel": int((da[pos] / ra[pos] > 1e-4).sum()),
+            "n_grad_over_1e-3_rel": int((dg[gpos] / gn[gpos] > 1e-3).sum()),
+            "n_over_stated_tolerances": int((da > 1e-4 * np.maximum(ra, 1.0)).sum()
+                                            + (dg > 1e-3 * np.maximum(gn, 1e-2)).sum())}
 
 
 def run_gpu(args):
@@ -182,67 +299,20 @@ def run_gpu(args):
     rad = torch.as_tensor(m.radii, dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def timed(precision, steps, warmup, grad=True):
-        ctx = api.Context(device=local, stream=stream, precision=precision)
-        a = torch.empty(n, dtype=torch.float64, device=dev)
-        g = torch.empty((n, 3), dtype=torch.float64, device=dev) if grad else None
-        with torch.cuda.stream(stream):
-            for _ in range(warmup):
-                ctx.compute(xyz, rad, a, g)
-            ctx.status_sync()
-            evs = []
-            k0 = api.kernel_launches()
-            for _ in range(steps):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                ctx.compute(xyz, rad, a, g)
-                e1.record(stream)
-                evs.append((e0, e1))
-            ctx.status_sync()
-        torch.cuda.synchronize(dev)
-        launches = api.kernel_launches() - k0
-        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-        ctx.close()
-        timed.launches = launches
-        return ms, a, g
-
-    def phases(precision, steps, grad=True):
-        """Mean device time per kernel phase: the same steps with CUDA events recorded between
-        the library's kernels (the events hold back the early launch of each next kernel, so
-        these steps are not the timed ones)."""
-        ctx = api.Context(device=local, stream=stream, precision=precision)
-        a = torch.empty(n, dtype=torch.float64, device=dev)
-        g = torch.empty((n, 3), dtype=torch.float64, device=dev) if grad else None
-        with torch.cuda.stream(stream):
-            ctx.compute(xyz, rad, a, g)
-            ctx.status_sync()
-            ctx.set_timing(True)
-            for _ in range(steps):
-                flush.zero_()
-                ctx.compute(xyz, rad, a, g)
-            ctx.status_sync()
-        torch.cuda.synchronize(dev)
-        ph, calls = ctx.kernel_times()
-        ctx.close()
-        return {k: v / max(calls, 1) for k, v in ph.items()}
+    tm = Timer(api, torch, dev, local, stream, flush)
+    pk = measure_peaks(local)
+    dpk = driver_peaks()
 
     # timed region: barrier, then K steps with CUDA events on the library's stream around each
-    # step; the per-kernel times (dominant kernel) come from the same number of steps right
-    # after, with events between the kernels
+    # step; the clock sampler runs over the timed steps and the per-kernel steps after them
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
-        t_wall0 = time.perf_counter()
-        ms_mixed, a_mix, g_mix = timed("mixed", args.steps, args.warmup)
-        launches_mixed = timed.launches
-        t_wall1 = time.perf_counter()
-    ms_fp64, a_64, g_64 = timed("fp64", max(3, args.steps // 2), args.warmup)
-    ph_mixed = phases("mixed", args.steps)
-    ph_fp64 = phases("fp64", max(3, args.steps // 2))
+        ms_mixed, a_mix, g_mix, launches_mixed = tm.steps(xyz, rad, "mixed", args.steps, args.warmup)
+        ph_mixed = tm.phases(xyz, rad, "mixed", args.steps)
+    ms_fp64, a_64, g_64, _ = tm.steps(xyz, rad, "fp64", max(3, args.steps // 2), args.warmup)
+    ph_fp64 = tm.phases(xyz, rad, "fp64", max(3, args.steps // 2))
     step_ms = sum(ms_mixed) / len(ms_mixed)
     value = replica_throughput(sum(ms_mixed) / 1e3, ws, n, args.steps, dev)
     fp64_value = n / (sum(ms_fp64) / len(ms_fp64) / 1e3)
@@ -296,7 +366,7 @@ def run_gpu(args):
     sr_ms = sum(e0.elapsed_time(e1) for e0, e1 in sev) / len(sev)
     sr_tf = ctx.sr_tests() * 9.0 / (sr_ms / 1e3) / 1e12
     shrake_rupley = {"points_per_sphere": 960, "ms_per_call": sr_ms, "atoms_per_s": n / sr_ms * 1e3,
-                     "achieved_tflops": sr_tf, "frac_of_fp32_peak": sr_tf / peaks()["fp32_tflops"],
+                     "achieved_tflops": sr_tf, "frac_of_fp32_roof": sr_tf / pk["fp32_tflops"],
                      "total_sasa": float(asr.sum().item()),
                      "note": "call time includes the cell-list build; 9 FP32 flop per point-neighbour test"}
     ctx.close()
@@ -319,37 +389,11 @@ def run_gpu(args):
         ctx.compute_host(hx, hr, out=(ha, hg))
         e2e.append(time.perf_counter() - t0)
     ctx.status_sync()
+    ctx.close()
     e2e_value = n / (sum(e2e) / len(e2e))
 
-    # work model from the complex the GPU path exports (outside the timed region)
-    ctx = api.Context(device=local, stream=stream)
-    with torch.cuda.stream(stream):
-        rec = ctx.export_complex(xyz, rad).cpu().numpy()
-    ctx.close()
-    fl_atom, inc = algorithmic_flops_per_atom(rec, n)
-    pk = peaks()
-    achieved_path = fl_atom * n / (step_ms / 1e3) / 1e12
-    traffic = measured_traffic()
-    # the dominant kernel (largest device time per step) and its algorithmic work: the cell
-    # kernel certifies the atom's star (FLOP_STAR_TET per star tetrahedron); the terms
-    # kernel evaluates the area terms and their gradient; the other phases do integer and
-    # topology work only (no term of the flop model)
-    fwd = fl_atom - FLOP_STAR_TET * STAR_TETS_PER_ATOM
-    phase_flop = {"cell": FLOP_STAR_TET * STAR_TETS_PER_ATOM * n, "terms": fwd * n}
-    dom = max(ph_mixed, key=lambda k: ph_mixed[k])
-    dom_ms = ph_mixed[dom]
-    # the kernel is bound by instruction issue: its warp instructions per launch (ncu) over its
-    # live duration, against 152 SMs x 4 schedulers x 1 instruction per cycle at the max clock
-    inst = measured_counters().get("warp_instructions_per_launch")
-    issue_peak = 152 * 4 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
-    issue = None
-    if inst and dom_ms > 0:
-        ach = inst / (dom_ms / 1e3) / 1e9
-        issue = {"warp_inst_per_launch": inst, "achieved_ginst_s": ach, "peak_ginst_s": issue_peak,
-                 "frac": ach / issue_peak,
-                 "source": "smsp__inst_executed.sum of one launch (profiles/traffic.json) / live duration"}
-    achieved = phase_flop.get(dom, 0.0) / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else 0.0
-    terms_tf = phase_flop["terms"] / (ph_mixed["terms"] / 1e3) / 1e12 if ph_mixed["terms"] > 0 else 0.0
+    wm = json.load(open(WORK_MODEL))
+    roofline, roofline_terms = roofline_block(wm, n, ph_mixed, pk, dpk, measured_counters())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -359,28 +403,27 @@ def run_gpu(args):
                        total_sasa=float(a_mix.sum().item()),
                        fp64_minus_mixed_total_rel=float((a_64.sum() - a_mix.sum()).item() / a_64.sum().item()),
                        volume=volume, shrake_rupley=shrake_rupley),
-        "roofline": {"bound": "alu", "kernel": f"k_atoms phase '{dom}'", "achieved": achieved,
-                     "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
-                     "traffic": traffic, "kernel_ms": dom_ms,
-                     "peak_source": "FP32 vector peak derived: 152 SMs x 128 lanes x 2 x max SM clock",
-                     "work_model_flop_per_launch": phase_flop.get(dom, 0.0), "issue": issue,
-                     "note": "achieved = algorithmic flop of the dominant kernel per launch / its mean "
-                             "CUDA-event duration (events between the library's kernels, over K steps of "
-                             "the same workload run right after the timed steps)"},
-        "roofline_terms": {"achieved": terms_tf, "frac": terms_tf / pk["fp32_tflops"], "kernel_ms": ph_mixed["terms"],
-                           "work_model_flop_per_launch": phase_flop["terms"]},
-        "roofline_path": {"achieved": achieved_path, "frac": achieved_path / pk["fp32_tflops"],
-                          "work_model_flop_per_atom": fl_atom, "complex_incidences_per_atom": inc,
-                          "note": "whole step (every kernel of the hot path)"},
+        "roofline": roofline,
+        "roofline_terms": roofline_terms,
+        "peaks_measured": pk,
         "phase_ms": {"mixed": ph_mixed, "fp64": ph_fp64},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 32 * n},
         "gpu_launches": launches_mixed,
         "clocks": clk.summary(),
     }
-    if rank == 0 and ws == 1 and not args.no_serving:
-        line["serving"] = serving_measure(512, 12, loads=(0.8,))
+    if rank == 0 and ws == 1 and not args.quick:
+        line["capsid"] = capsid_measure(args, tm, wm, pk)
+        line["trajectory"] = trajectory_measure(args, local)
+        with ClockSampler(local) as sclk:
+            line["serving"] = serving_measure(4096, 32, loads=(0.5, 0.8, 0.95))
+        line["serving"]["clocks"] = sclk.summary()
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(m)
+        base, ref = cpu_baseline(m)
+        line["cpu_baseline"] = base
+        line["accuracy_vs_oracle"] = {"mixed": accuracy(ref[0], ref[1], a_mix.cpu().numpy(), g_mix.cpu().numpy()),
+                                      "fp64": accuracy(ref[0], ref[1], a_64.cpu().numpy(), g_64.cpu().numpy()),
+                                      "tolerances": "per atom |dA| <= 1e-4 max(A, 1 A^2); total 1e-6; "
+                                                    "|dg| <= 1e-3 max(|g|, 1e-2)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -388,16 +431,112 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def capsid_measure(args, tm, wm, pk):
+    """The 1,000,000-atom capsid-like shell (inputs larger than L2), mixed vs FP64, SASA +
+    gradient; the dominant (split) cell kernel's roofline with the globule's per-atom work
+    model, and its DRAM traffic per atom when an ncu record of that kernel exists."""
+    import torch
+    from paper_2401_10462_gb300 import inputs
+    m = inputs.make("shell", 1_000_000, 0)
+    xyz = torch.as_tensor(m.coords, device=tm.dev)
+    rad = torch.as_tensor(m.radii, device=tm.dev)
+    res = {"workload": "capsid shell 1,000,000 atoms, seed 0", "outer_radius_A": m.extent,
+           "density_per_A3": m.density(), "inputs_larger_than_L2": True}
+    with ClockSampler(tm.local) as clk:
+        ms, a, _, _ = tm.steps(xyz, rad, "mixed", max(3, args.steps // 2), 2)
+        ph = tm.phases(xyz, rad, "mixed", 3)
+    res["clocks"] = clk.summary()
+    ms64, a64, _, _ = tm.steps(xyz, rad, "fp64", 3, 1)
+    t = sum(ms) / len(ms)
+    t64 = sum(ms64) / len(ms64)
+    res.update({"mixed": {"ms_per_step": t, "atoms_per_s": m.n / t * 1e3, "total_sasa": float(a.sum().item())},
+                "fp64": {"ms_per_step": t64, "atoms_per_s": m.n / t64 * 1e3, "total_sasa": float(a64.sum().item())},
+                "mixed_over_fp64": t64 / t, "phase_ms": ph,
+                "fp64_minus_mixed_total_rel": float((a64.sum() - a.sum()).item() / a64.sum().item())})
+    cnt = measured_counters("traffic_capsid.json")
+    rl, _ = roofline_block(wm, m.n, ph, pk, driver_peaks(), cnt)
+    rl["work_model"] += " (per-atom counts of the 5,000-atom globule, same placement rules)"
+    rl["traffic_bytes_per_atom"] = (cnt["bytes_per_launch"] / m.n) if cnt.get("bytes_per_launch") else None
+    res["roofline"] = rl
+    return res
+
+
+def trajectory_measure(args, local):
+    """20,000-atom globule, E_np through the autograd Function, Gaussian steps (sigma 0.01 A)
+    replayed from one captured CUDA graph, without and with Verlet-skin lists."""
+    import torch
+    from paper_2401_10462_gb300 import autograd as ag, inputs
+    m = inputs.make("globule", 20000, 0)
+    dev = torch.device("cuda", local)
+    out = {"workload": "graphed trajectory, 20,000-atom globule, sigma 0.01 A"}
+    for skin in (0.0, 1.0):
+        tr = ag.GraphedTrajectory(torch.as_tensor(m.coords, device=dev), torch.as_tensor(m.radii, device=dev),
+                                  sigma=0.01, seed=0, skin=skin).capture()
+        tr.replay(args.warmup)
+        torch.cuda.synchronize()
+        steps = max(args.steps, 200)
+        with ClockSampler(local) as clk:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tr.replay(steps)      # replays on the trajectory stream, joined back to the current one
+            e1.record()
+            torch.cuda.synchronize()
+        tr.check()
+        ms = e0.elapsed_time(e1) / steps
+        out[f"skin_{skin:g}"] = {"steps": steps, "ms_per_step": ms, "atoms_per_s": m.n / ms * 1e3,
+                                 "energy_kcal_mol": tr.energy.item(), "clocks": clk.summary()}
+    return out
+
+
+def host_info():
+    model = platform.processor() or platform.machine()
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in txt.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
 def cpu_baseline(m):
-    """The oracle as it stands (single-threaded C++, exact predicates) on the same molecule."""
+    """The oracle as it stands on the GPU machine's host: single-threaded end to end (triangulation
+    + complex + areas + gradient) on the 304- and 5,000-atom globules and a 20,000-atom one,
+    and its area and gradient stage on all cores (OpenMP; the triangulation stays serial);
+    1,000,000 atoms extrapolated as n log n from the 20,000-atom time.  Returns the record and
+    the oracle's areas and gradient of the 5,000-atom workload."""
     from oracle import oracle
+    from paper_2401_10462_gb300 import inputs
     oracle.build()
-    t0 = time.perf_counter()
-    o = oracle.Oracle(m.coords, m.radii)
-    o.areas(grad=True)
-    dt = time.perf_counter() - t0
-    return {"value": m.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"the full workload ({m.n} atoms, one step: triangulation + complex + areas + gradient), {dt:.1f} s"}
+    info = host_info()
+    sizes = {}
+    ref = None
+    for name, mol in (("globule304", inputs.globule(304, 0)), ("globule5000", m), ("globule20000", inputs.make("globule", 20000, 0))):
+        t0 = time.perf_counter()
+        o = oracle.Oracle(mol.coords, mol.radii)
+        t1 = time.perf_counter()
+        a, _, g = o.areas(grad=True)
+        t2 = time.perf_counter()
+        _, _, _, used = o.areas_parallel(info["nproc"] or 1)
+        t3 = time.perf_counter()
+        sizes[name] = {"n_atoms": mol.n, "single_thread_s": t2 - t0, "single_thread_atoms_per_s": mol.n / (t2 - t0),
+                       "triangulation_and_complex_s": t1 - t0, "area_gradient_stage_1_thread_s": t2 - t1,
+                       "area_gradient_stage_all_cores_s": t3 - t2, "threads": used}
+        if mol is m:
+            ref = (a, g)
+    t20 = sizes["globule20000"]["single_thread_s"]
+    ext = t20 * (1e6 * math.log(1e6)) / (2e4 * math.log(2e4))
+    sizes["capsid1000000_extrapolated"] = {"n_atoms": 1_000_000, "single_thread_s": ext,
+                                           "single_thread_atoms_per_s": 1e6 / ext,
+                                           "note": "extrapolated as n log n from the 20,000-atom time, not measured"}
+    head = sizes["globule5000"]
+    rec = {"value": head["single_thread_atoms_per_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"the full 5,000-atom workload, one pass (triangulation + complex + areas + gradient), "
+                     f"{head['single_thread_s']:.1f} s on one core; sizes and the all-core area stage below",
+           "host": info, "sizes": sizes}
+    return rec, ref
 
 
 def run_reference(args):
@@ -408,27 +547,23 @@ def run_reference(args):
     from paper_2401_10462_gb300 import inputs
     oracle.build()
     m = inputs.globule(N_ATOMS, SEED)
-    # each step is the oracle on a bounded sample of the workload: the atoms within a
-    # patch around a seeded set of centres (about 5 s of CPU work per step)
-    rng = np.random.default_rng(0)
-    times, atoms = [], 0
+    # every step is one full oracle pass over the same 5,000-atom workload (about 3-4 s)
+    times = []
     for s in range(args.warmup + args.steps):
-        centres = rng.choice(m.n, 8, replace=False)
-        idx = oracle.local_patch(m.coords, m.radii, centres, cutoff=14.0)
         t0 = time.perf_counter()
-        o = oracle.Oracle(m.coords[idx], m.radii[idx])
+        o = oracle.Oracle(m.coords, m.radii)
         o.areas(grad=True)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
-            atoms += len(idx)
-    value = atoms / sum(times)
+    value = m.n * len(times) / sum(times)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+exact", "data": "synthetic",
             "config": dict(WORKLOAD), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step: the oracle on the atoms within 14 A of 8 seeded atoms of the workload"},
+                             "sample": "per step: one full oracle pass over the 5,000-atom workload",
+                             "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -447,7 +582,7 @@ def serving_measure(count: int, pool: int, loads=(0.8,), seed: int = 0, slots: i
     sat = srv.run(reqs, realtime=False)
     mu = sat["requests_per_s"]
     out = {"requests": count, "pool_molecules": pool, "slots": slots, "saturated_requests_per_s": mu,
-           "saturated_atoms_per_s": sat["atoms_per_s"], "loads": []}
+           "saturated_atoms_per_s": sat["atoms_per_s"], "failed": sat["failed"], "loads": []}
     for ld in loads:
         t = inputs.poisson_arrivals(count, ld * mu, seed=seed + 11)
         for r, ti in zip(reqs, t):
@@ -455,69 +590,9 @@ def serving_measure(count: int, pool: int, loads=(0.8,), seed: int = 0, slots: i
             r.done = None
         st = srv.run(reqs, realtime=True)
         out["loads"].append({"lambda_over_mu": ld, "lambda_requests_per_s": ld * mu, "p50_ms": st["p50_ms"],
-                             "p99_ms": st["p99_ms"], "atoms_per_s": st["atoms_per_s"]})
+                             "p99_ms": st["p99_ms"], "atoms_per_s": st["atoms_per_s"], "failed": st["failed"]})
     srv.close()
     return out
-
-
-def run_capsid(args):
-    """The 1,000,000-atom capsid-like shell, mixed vs FP64, SASA + gradient."""
-    import torch
-    from paper_2401_10462_gb300 import api, inputs
-    m = inputs.make("shell", 1_000_000, 0)
-    dev = torch.device("cuda", 0)
-    xyz = torch.as_tensor(m.coords, device=dev)
-    rad = torch.as_tensor(m.radii, device=dev)
-    stream = torch.cuda.Stream(device=dev)
-    res = {}
-    for prec, steps in (("mixed", args.steps), ("fp64", max(1, args.steps // 2))):
-        ctx = api.Context(stream=stream, precision=prec)
-        a = torch.empty(m.n, dtype=torch.float64, device=dev)
-        g = torch.empty((m.n, 3), dtype=torch.float64, device=dev)
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                ctx.compute(xyz, rad, a, g)
-            ctx.status_sync()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(steps):
-                ctx.compute(xyz, rad, a, g)
-            e1.record(stream)
-            ctx.status_sync()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        res[prec] = {"ms_per_step": ms, "atoms_per_s": m.n / ms * 1e3, "total_sasa": float(a.sum().item())}
-        ctx.close()
-    print(json.dumps({"workload": "capsid shell 1,000,000 atoms", "outer_radius_A": m.extent,
-                      "density_per_A3": m.density(), "inputs_larger_than_L2": True, **res,
-                      "mixed_over_fp64": res["mixed"]["atoms_per_s"] / res["fp64"]["atoms_per_s"]}), flush=True)
-
-
-def run_trajectory(args):
-    """Trajectory: 20,000-atom globule, E_np through the autograd Function, Gaussian steps
-    (sigma 0.01 A) replayed from one captured CUDA graph; reports ms per graphed step without
-    and with Verlet-skin lists (skin 1 A: rebuilt on the device once an atom moved 0.5 A)."""
-    import torch
-    from paper_2401_10462_gb300 import autograd as ag, inputs
-    m = inputs.make("globule", 20000, 0)
-    dev = torch.device("cuda", 0)
-    out = {"workload": "graphed trajectory, 20,000-atom globule"}
-    for skin in (0.0, 1.0):
-        tr = ag.GraphedTrajectory(torch.as_tensor(m.coords, device=dev), torch.as_tensor(m.radii, device=dev),
-                                  sigma=0.01, seed=0, skin=skin).capture()
-        tr.replay(args.warmup)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        steps = max(args.steps, 100)
-        e0.record()
-        tr.replay(steps)      # replays on the trajectory stream, joined back to the current one
-        e1.record()
-        torch.cuda.synchronize()
-        tr.check()
-        ms = e0.elapsed_time(e1) / steps
-        out[f"skin_{skin:g}"] = {"steps": steps, "ms_per_step": ms, "atoms_per_s": m.n / ms * 1e3,
-                                 "energy_kcal_mol": tr.energy.item()}
-    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -526,23 +601,31 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="globule5k", choices=["globule5k", "capsid", "trajectory", "serving"])
+    ap.add_argument("--workload", default="all", choices=["all", "capsid", "trajectory", "serving"])
+    ap.add_argument("--quick", action="store_true", help="headline workload only (no capsid, trajectory, serving)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "capsid":
-        run_capsid(args)
+        return
+    if args.workload == "all":
+        run_gpu(args)
+        return
+    import torch
+    from paper_2401_10462_gb300 import api
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tm = Timer(api, torch, dev, 0, stream, flush)
+    if args.workload == "capsid":
+        print(json.dumps(capsid_measure(args, tm, json.load(open(WORK_MODEL)), measure_peaks(0))), flush=True)
     elif args.workload == "trajectory":
-        run_trajectory(args)
-    elif args.workload == "serving":
+        print(json.dumps(trajectory_measure(args, 0)), flush=True)
+    else:
         print(json.dumps({"workload": "serving stream, 4,096 requests of 300-50,000 atoms",
                           **serving_measure(4096, 32, loads=(0.5, 0.8, 0.95))}), flush=True)
-    else:
-        run_gpu(args)
 
 
 if __name__ == "__main__":

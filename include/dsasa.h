@@ -51,8 +51,10 @@ typedef enum {
     DSASA_ERR_UNRESOLVED = 4,    /* an exact predicate exceeded its expansion capacity */
     DSASA_ERR_CUDA = 5,          /* a CUDA runtime call failed (see dsasa_last_error) */
     DSASA_ERR_UNIMPLEMENTED = 6,
-    DSASA_ERR_DEGENERATE = 7,    /* an exactly degenerate input (tie) was met; outputs valid
-                                    for one consistent tie-break only */
+    DSASA_ERR_DEGENERATE = 7,    /* a tie that Simulation of Simplicity cannot break was met
+                                    (coincident atoms); exact ties of co-spherical or
+                                    co-planar atoms are broken as the regular triangulation
+                                    breaks them and are not errors */
     DSASA_ERR_INPUT = 8          /* non-finite coordinate or radius found on the device */
 } dsasa_status;
 

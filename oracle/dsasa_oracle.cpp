@@ -539,11 +539,34 @@ struct Areas {
     long n_tri_bad = 0;
 };
 
-static void compute_areas(const Result& res, const double* w, bool want_grad, Areas& out) {
+// Exterior classification shared by the term loops (the sums of Eq. sainexclu run over the
+// boundary of C): a vertex / edge whose every triangulation tetrahedron is in C has
+// coefficient 0; ntet counts the tetrahedra of C on each triangle.
+struct TermPrep {
+    std::vector<int> kstar;
+    std::map<std::array<int, 2>, int> kedge;
+    std::map<std::array<int, 3>, int> ntet;
+};
+
+static void prepare_terms(const Result& res, TermPrep& p) {
+    p.kstar.assign(res.n, 0);
+    for (auto& T : res.kT)
+        for (int s = 0; s < 4; ++s) {
+            p.kstar[T[s]] += 1;
+            for (int t = s + 1; t < 4; ++t) p.kedge[{T[s], T[t]}] += 1;
+            std::array<int, 3> f;
+            int m = 0;
+            for (int j = 0; j < 4; ++j) if (j != s) f[m++] = T[j];
+            p.ntet[f] += 1;
+        }
+}
+
+// The terms of Eq. (sainexclu) and, if want_grad, their gradient (Eq. inexclu): the share
+// `part` of `nparts` of the vertices, tetrahedra, edges and triangles of C (every nparts-th
+// one; part 0 of 1 is all of them in order), added to out (sized by the caller).
+static void accumulate_terms(const Result& res, const TermPrep& p, const double* w, bool want_grad, Areas& out,
+                             int part, int nparts) {
     const Geo& g = res.g;
-    int n = res.n;
-    out.A.assign(n, 0.0L);
-    out.G.assign(want_grad ? 3 * n : 0, 0.0);
     auto W = [&](int i) { return w ? w[i] : 1.0; };
     auto pt = [&](int i) { return &g.pts[i].x; };
     auto R = [&](int i) { return g.pts[i].R; };
@@ -555,26 +578,20 @@ static void compute_areas(const Result& res, const double* w, bool want_grad, Ar
         for (int s = 0; s < m; ++s)
             for (int k = 0; k < 3; ++k) out.G[3 * ids[s] + k] += wo * val.d[3 * s + k];
     };
-    // exterior classification (the sums of Eq. sainexclu run over the boundary of C): a
-    // vertex / edge whose every triangulation tetrahedron is in C has coefficient 0
-    std::vector<int> kstar(n, 0);
-    std::map<std::array<int, 2>, int> kedge;
-    for (auto& T : res.kT)
-        for (int s = 0; s < 4; ++s) {
-            kstar[T[s]] += 1;
-            for (int t = s + 1; t < 4; ++t) kedge[{T[s], T[t]}] += 1;
-        }
-    auto vert_interior = [&](int i) { return kstar[i] == res.star_all[i]; };
+    auto vert_interior = [&](int i) { return p.kstar[i] == res.star_all[i]; };
     auto edge_interior = [&](int a, int b) {
         std::array<int, 2> e = {std::min(a, b), std::max(a, b)};
-        auto it = kedge.find(e);
-        return it != kedge.end() && it->second == res.edge_star_all.at(e);
+        auto it = p.kedge.find(e);
+        return it != p.kedge.end() && it->second == res.edge_star_all.at(e);
     };
     // vertex constant part 4 pi R^2
-    for (int i : res.kv)
+    for (size_t q = part; q < res.kv.size(); q += nparts) {
+        int i = res.kv[q];
         if (!vert_interior(i)) out.A[i] += (long double)(4.0 * PI * R(i) * R(i));
+    }
     // tetrahedra: -4 pi R_v^2 omega_v(T) for each vertex, +cap_u(v) phi_uv(T) for each edge/direction
-    for (auto& T : res.kT) {
+    for (size_t q = part; q < res.kT.size(); q += nparts) {
+        auto& T = res.kT[q];
         DV P[4];
         for (int s = 0; s < 4; ++s) P[s] = seed_point(pt(T[s]), s);
         for (int s = 0; s < 4; ++s) {
@@ -593,7 +610,8 @@ static void compute_areas(const Result& res, const double* w, bool want_grad, Ar
         }
     }
     // edges: -cap_i(j) for both directions
-    for (auto& E : res.ke) {
+    for (size_t q = part; q < res.ke.size(); q += nparts) {
+        auto& E = res.ke[q];
         if (edge_interior(E[0], E[1])) continue;
         for (int s = 0; s < 2; ++s) {
             int i = E[s], j = E[1 - s];
@@ -603,16 +621,10 @@ static void compute_areas(const Result& res, const double* w, bool want_grad, Ar
         }
     }
     // triangles: c_ijk S_ijk^(i) with c = 1 - #coface tetrahedra in C / 2
-    std::map<std::array<int, 3>, int> ntet;
-    for (auto& T : res.kT)
-        for (int s = 0; s < 4; ++s) {
-            std::array<int, 3> f;
-            int m = 0;
-            for (int j = 0; j < 4; ++j) if (j != s) f[m++] = T[j];
-            ntet[f] += 1;
-        }
-    for (auto& F : res.kt) {
-        double cc = 1.0 - 0.5 * (ntet.count(F) ? ntet[F] : 0);
+    for (size_t q = part; q < res.kt.size(); q += nparts) {
+        auto& F = res.kt[q];
+        auto it = p.ntet.find(F);
+        double cc = 1.0 - 0.5 * (it != p.ntet.end() ? it->second : 0);
         if (cc == 0.0) continue;
         for (int s = 0; s < 3; ++s) {
             int i = F[s], j = F[(s + 1) % 3], k = F[(s + 2) % 3];
@@ -623,6 +635,81 @@ static void compute_areas(const Result& res, const double* w, bool want_grad, Ar
             int ids[3] = {i, j, k};
             add(i, S, ids, 3);
         }
+    }
+}
+
+static void compute_areas(const Result& res, const double* w, bool want_grad, Areas& out) {
+    out.A.assign(res.n, 0.0L);
+    out.G.assign(want_grad ? 3 * res.n : 0, 0.0);
+    TermPrep p;
+    prepare_terms(res, p);
+    accumulate_terms(res, p, w, want_grad, out, 0, 1);
+}
+
+// The same terms split over `nthreads` OpenMP threads (timing of the area and gradient stage
+// on all host cores; the triangulation stays serial).  Each thread sums its share, the
+// shares are added in thread order: the values equal compute_areas' up to the order of
+// summation.
+static void compute_areas_parallel(const Result& res, const double* w, bool want_grad, Areas& out, int nthreads) {
+    out.A.assign(res.n, 0.0L);
+    out.G.assign(want_grad ? 3 * res.n : 0, 0.0);
+    TermPrep p;
+    prepare_terms(res, p);
+    std::vector<Areas> parts(nthreads);
+#pragma omp parallel for num_threads(nthreads) schedule(static, 1)
+    for (int t = 0; t < nthreads; ++t) {
+        parts[t].A.assign(res.n, 0.0L);
+        parts[t].G.assign(want_grad ? 3 * res.n : 0, 0.0);
+        accumulate_terms(res, p, w, want_grad, parts[t], t, nthreads);
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        for (int i = 0; i < res.n; ++i) out.A[i] += parts[t].A[i];
+        for (size_t k = 0; k < out.G.size(); ++k) out.G[k] += parts[t].G[k];
+        out.n_tri_bad += parts[t].n_tri_bad;
+    }
+}
+
+// Numbers of the terms compute_areas evaluates (the same loops, counting instead of
+// evaluating): out[0] vertex constants 4 pi R^2, out[1] solid-angle terms omega, out[2]
+// dihedral terms phi (each with its cap factor), out[3] edge caps, out[4] triangle terms
+// S_ijk^(i); used for the benchmark's work model.
+static void count_terms(const Result& res, long* out) {
+    int n = res.n;
+    for (int k = 0; k < 5; ++k) out[k] = 0;
+    std::vector<int> kstar(n, 0);
+    std::map<std::array<int, 2>, int> kedge;
+    for (auto& T : res.kT)
+        for (int s = 0; s < 4; ++s) {
+            kstar[T[s]] += 1;
+            for (int t = s + 1; t < 4; ++t) kedge[{T[s], T[t]}] += 1;
+        }
+    auto vert_interior = [&](int i) { return kstar[i] == res.star_all[i]; };
+    auto edge_interior = [&](int a, int b) {
+        std::array<int, 2> e = {std::min(a, b), std::max(a, b)};
+        auto it = kedge.find(e);
+        return it != kedge.end() && it->second == res.edge_star_all.at(e);
+    };
+    for (int i : res.kv)
+        if (!vert_interior(i)) out[0] += 1;
+    for (auto& T : res.kT)
+        for (int s = 0; s < 4; ++s) {
+            if (!vert_interior(T[s])) out[1] += 1;
+            for (int v = 0; v < 4; ++v)
+                if (v != s && !edge_interior(T[s], T[v])) out[2] += 1;
+        }
+    for (auto& E : res.ke)
+        if (!edge_interior(E[0], E[1])) out[3] += 2;
+    std::map<std::array<int, 3>, int> ntet;
+    for (auto& T : res.kT)
+        for (int s = 0; s < 4; ++s) {
+            std::array<int, 3> f;
+            int m = 0;
+            for (int j = 0; j < 4; ++j) if (j != s) f[m++] = T[j];
+            ntet[f] += 1;
+        }
+    for (auto& F : res.kt) {
+        double cc = 1.0 - 0.5 * (ntet.count(F) ? ntet[F] : 0);
+        if (cc != 0.0) out[4] += 3;
     }
 }
 
@@ -974,6 +1061,8 @@ void oracle_counts(const OracleHandle* h, long* out) {
 
 void oracle_times(const OracleHandle* h, double* out) { out[0] = h->res.t_rt; out[1] = h->res.t_alpha; }
 
+void oracle_term_counts(const OracleHandle* h, long* out) { count_terms(h->res, out); }
+
 // dim 0..3: the dual complex's simplices (sorted tuples, lexicographic); dim 4: all
 // triangulation tetrahedra with four atoms
 void oracle_simplices(const OracleHandle* h, int dim, int* out) {
@@ -995,6 +1084,25 @@ void oracle_redundant(const OracleHandle* h, unsigned char* out) {
 long oracle_areas(const OracleHandle* h, const double* weights, double* areas, double* grad, double* total) {
     Areas a;
     compute_areas(h->res, weights, grad != nullptr, a);
+    long double tot = 0;
+    for (int i = 0; i < h->res.n; ++i) { areas[i] = (double)a.A[i]; tot += a.A[i]; }
+    if (total) *total = (double)tot;
+    if (grad) for (int k = 0; k < 3 * h->res.n; ++k) grad[k] = a.G[k];
+    return a.n_tri_bad;
+}
+
+// as oracle_areas with the term loops on nthreads OpenMP threads (timing only); returns the
+// number of threads the build supports in *used (1 without OpenMP)
+long oracle_areas_parallel(const OracleHandle* h, const double* weights, double* areas, double* grad, double* total,
+                           int nthreads, int* used) {
+#ifdef _OPENMP
+    const int t = nthreads > 0 ? nthreads : 1;
+#else
+    const int t = 1;
+#endif
+    if (used) *used = t;
+    Areas a;
+    compute_areas_parallel(h->res, weights, grad != nullptr, a, t);
     long double tot = 0;
     for (int i = 0; i < h->res.n; ++i) { areas[i] = (double)a.A[i]; tot += a.A[i]; }
     if (total) *total = (double)tot;

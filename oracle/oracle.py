@@ -34,7 +34,11 @@ def build(force: bool = False) -> str:
     newest = max(os.path.getmtime(s) for s in _SRC)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC[0]])
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC[0]]
+        try:   # OpenMP only serves the timing of the area stage on all cores
+            subprocess.check_call(cmd[:1] + ["-fopenmp"] + cmd[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(cmd)
         os.replace(tmp, _SO)
     return _SO
 
@@ -52,10 +56,13 @@ def _load():
             lib.oracle_free.argtypes = [ctypes.c_void_p]
             lib.oracle_counts.argtypes = [ctypes.c_void_p, lp]
             lib.oracle_times.argtypes = [ctypes.c_void_p, dp]
+            lib.oracle_term_counts.argtypes = [ctypes.c_void_p, lp]
             lib.oracle_simplices.argtypes = [ctypes.c_void_p, ctypes.c_int, ip]
             lib.oracle_redundant.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ubyte)]
             lib.oracle_areas.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
             lib.oracle_areas.restype = ctypes.c_long
+            lib.oracle_areas_parallel.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, ctypes.c_int, ip]
+            lib.oracle_areas_parallel.restype = ctypes.c_long
             lib.oracle_volumes.argtypes = [ctypes.c_void_p, dp, dp, dp]
             lib.oracle_volumes.restype = ctypes.c_long
             lib.oracle_gauss_bonnet.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
@@ -108,6 +115,14 @@ class Oracle:
         self._lib.oracle_times(self._h, out)
         return {"triangulation_s": out[0], "alpha_s": out[1]}
 
+    TERM_KEYS = ("vertex_constants", "solid_angles", "dihedrals", "edge_caps", "triangles")
+
+    def term_counts(self) -> dict:
+        """Numbers of the terms of Eq. (sainexclu) the area computation evaluates."""
+        out = (ctypes.c_long * 5)()
+        self._lib.oracle_term_counts(self._h, out)
+        return dict(zip(self.TERM_KEYS, list(out)))
+
     def simplices(self, dim: int) -> np.ndarray:
         """dim 0..3: the dual complex C (sorted tuples); dim 4: all triangulation tetrahedra."""
         c = self.counts()
@@ -136,6 +151,19 @@ class Oracle:
             raise RuntimeError(f"{bad} triangles of C without a triple point")
         return a[: self.n], tot.value, (g[: self.n] if g is not None else None)
 
+
+    def areas_parallel(self, threads: int, grad: bool = True):
+        """areas() with the term loops on `threads` OpenMP threads (for timing the area and
+        gradient stage on all cores); returns (areas, total, grad, threads used)."""
+        a = np.zeros(max(self.n, 1))
+        g = np.zeros((max(self.n, 1), 3)) if grad else None
+        tot = ctypes.c_double(0)
+        used = ctypes.c_int(1)
+        bad = self._lib.oracle_areas_parallel(self._h, None, _d(a), _d(g) if g is not None else None,
+                                              ctypes.byref(tot), int(threads), ctypes.byref(used))
+        if bad:
+            raise RuntimeError(f"{bad} triangles of C without a triple point")
+        return a[: self.n], tot.value, (g[: self.n] if g is not None else None), used.value
 
     def volumes(self, grad: bool = True):
         """Per-atom volumes vol(B_i cap L_i), their total (the union volume) and

@@ -1,6 +1,7 @@
-"""In-tree build of libdsasa.so (CUDA, sm_103a) with nvcc.
+"""In-tree build of libdsasa.so (CUDA, sm_103a) with nvcc, and of libdsasa_peaks.so (the
+arithmetic-roof microbenchmarks that bench.py reports beside the kernels).
 
-Each translation unit is compiled in parallel, then linked into one shared library with
+Each translation unit is compiled in parallel, then linked into the shared libraries with
 the CUDA runtime linked statically.  No CMake, no torch extension machinery."""
 from __future__ import annotations
 
@@ -13,10 +14,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdsasa.so")
+PEAKS_LIB = os.path.join(BUILD, "libdsasa_peaks.so")   # arithmetic-roof microbenchmarks (bench.py)
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 UNITS = ["dsasa_grid.cu", "dsasa_atoms_f32.cu", "dsasa_atoms_f64.cu", "dsasa_capi.cu", "dsasa_noalloc.cu", "dsasa_sr.cu"]
+PEAK_UNITS = ["dsasa_peaks.cu"]
 
 
 def nvcc() -> str:
@@ -32,9 +35,9 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(PEAKS_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAKS_LIB))
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -44,10 +47,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    procs, objs = [], []
-    for u in UNITS:
+    procs, objs, pobjs = [], [], []
+    for u in UNITS + PEAK_UNITS:
         obj = os.path.join(BUILD, u.replace(".cu", ".o"))
-        objs.append(obj)
+        (pobjs if u in PEAK_UNITS else objs).append(obj)
         cmd = [cc, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, u), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -61,9 +64,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             print(out.decode(errors="replace"))
     if errs:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
+    for lib, o in ((LIB, objs), (PEAKS_LIB, pobjs)):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *o])
+        os.replace(tmp, lib)
     return LIB
 
 

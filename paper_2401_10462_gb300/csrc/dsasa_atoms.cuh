@@ -150,6 +150,40 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
+// A lane's sum of gradient contributions.  In the FP32 form it is a float-float sum: the
+// contributions gathered for one atom largely cancel, and a plain float sum would carry an
+// error of about 2^-24 times the largest partial sum, which moreover depends on the summation
+// order; with float-float the result depends on the contributions only.  The FP64 form sums in
+// double.
+template <class R> struct GAcc;
+template <> struct GAcc<float> {
+    FF x{0.f, 0.f}, y{0.f, 0.f}, z{0.f, 0.f};
+    __device__ __forceinline__ void add(float a, float b, float c) {
+        x = ff_add_f(x, a);
+        y = ff_add_f(y, b);
+        z = ff_add_f(z, c);
+    }
+    // warp sum (every lane ends with the same value: the float-float sum is commutative)
+    __device__ __forceinline__ void reduce(double& gx, double& gy, double& gz) {
+        for (int o = 16; o > 0; o >>= 1) {
+            x = ff_add(x, FF{__shfl_xor_sync(FULL, x.h, o), __shfl_xor_sync(FULL, x.l, o)});
+            y = ff_add(y, FF{__shfl_xor_sync(FULL, y.h, o), __shfl_xor_sync(FULL, y.l, o)});
+            z = ff_add(z, FF{__shfl_xor_sync(FULL, z.h, o), __shfl_xor_sync(FULL, z.l, o)});
+        }
+        gx = ff_to_double(x);
+        gy = ff_to_double(y);
+        gz = ff_to_double(z);
+    }
+};
+template <> struct GAcc<double> {
+    double x = 0.0, y = 0.0, z = 0.0;
+    __device__ __forceinline__ void add(double a, double b, double c) { x += a; y += b; z += c; }
+    __device__ __forceinline__ void reduce(double& gx, double& gy, double& gz) {
+        gx = warp_sum_d(x);
+        gy = warp_sum_d(y);
+        gz = warp_sum_d(z);
+    }
+};
 __device__ __forceinline__ uint8_t tv_get(const uchar4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 template <class SM> __device__ __forceinline__ void ta_set(SM* S, int t, int k, uint8_t s) {
     ((uint8_t*)&S->ta[t & (SM::kNT - 1)])[k] = s;
@@ -207,8 +241,11 @@ __device__ __forceinline__ int kind_planes(int kind) {
     return kind == PK_CLIP ? 4 : (kind == PK_TET || kind == PK_TRIB) ? 3 : (kind == PK_TRI || kind == PK_EDGEB) ? 2 : 1;
 }
 
-// Slow path: FP64 filter (unless skip64), then exact expansions.  Never returns an
-// undecided sign except for an exact zero (a tie, reported as degenerate).
+// Slow path: FP64 filter (unless skip64), then exact expansions.  An exact zero of the clip
+// test (a vertex exactly on a bisector: co-spherical atoms) is broken by Simulation of
+// Simplicity on the weights, as the regular triangulation breaks its ties (sos_clip_sign);
+// an exact zero of a test of the dual complex (psi = 0, an orthocentre exactly on a plane) is
+// a decision of its own (psi <= 0 is in C; "beyond" is strict) and is returned as 0.
 __device__ __noinline__ int resolve_exact(const Ctx& c, int kind, int g0, int g1, int g2, int g3, bool try64) {
     int gs[4] = {g0, g1, g2, g3};
     int np = kind_planes(kind);
@@ -228,7 +265,10 @@ __device__ __noinline__ int resolve_exact(const Ctx& c, int kind, int g0, int g1
         return v.n ? (v.c[v.n - 1] > 0 ? 1 : -1) : 0;
     }
     int s = xp_sign(v);
-    if (s == 0) atomicOr(c.status, ST_DEGENERATE);
+    if (s == 0 && kind == PK_CLIP) {
+        s = sos_clip_sign(P, gs, c.i);
+        if (s == 0) atomicOr(c.status, ST_DEGENERATE);   // coincident atoms: no perturbation separates them
+    }
     return s;
 }
 
@@ -1082,7 +1122,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         const R zero = (R)0;
         const double TWO_PI = 6.283185307179586476925;
         double area_acc = 0.0;
-        R gx = zero, gy = zero, gz = zero;
+        GAcc<R> gacc;
         const double wi_w = A.w ? A.w[i] : 1.0;
         const R wif = (R)wi_w;
         // Mixed mode: the radius quantities (R, R^2, R_i -+ R_j, 2 pi) enter as float pairs and
@@ -1128,9 +1168,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 const R kap = -(wif * Rr * ti + waf * Raf * ta);
                 // cap derivatives (Eq. edge): -Phi (2 pi / d)(w_i R_i t_a + w_a R_a t_i) u
                 const R cf = -phi * (R)TWO_PI / (dr * dr) * (wif * Rr * ta + waf * Raf * ti);
-                gx += kap * gsum.x + cf * pa.x;
-                gy += kap * gsum.y + cf * pa.y;
-                gz += kap * gsum.z + cf * pa.z;
+                gacc.add(kap * gsum.x + cf * pa.x, kap * gsum.y + cf * pa.y, kap * gsum.z + cf * pa.z);
             }
         };
         if constexpr (PH != PH_TERMS) {
@@ -1391,9 +1429,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                         P3<R> gc = dihedral_grad_c_ol(pa, pb, O, ppos(S, x), on_t ? (R)1 : (R)-1);
                         sx += kap * gc.x; sy += kap * gc.y; sz += kap * gc.z;
                     }
-                    gx += sx;
-                    gy += sy;
-                    gz += sz;
+                    gacc.add(sx, sy, sz);
                 }
             }
         }
@@ -1407,24 +1443,10 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 tot = ff_add(tot, FF{__shfl_xor_sync(FULL, tot.h, o), __shfl_xor_sync(FULL, tot.l, o)});
             for (int o = 16; o > 0; o >>= 1) cf_sum += __shfl_xor_sync(FULL, cf_sum, o);
             area_acc = ff_to_double(tot) + ((double)cf_sum + (double)vtx_const) * TWO_PI * c.Ri * c.Ri;
-            if (GRAD) {
-                for (int o = 16; o > 0; o >>= 1) {
-                    gx += __shfl_xor_sync(FULL, gx, o);
-                    gy += __shfl_xor_sync(FULL, gy, o);
-                    gz += __shfl_xor_sync(FULL, gz, o);
-                }
-                gxd = (double)gx;
-                gyd = (double)gy;
-                gzd = (double)gz;
-            }
         } else {
             area_acc = warp_sum_d(area_acc);
-            if (GRAD) {
-                gxd = warp_sum_d((double)gx);
-                gyd = warp_sum_d((double)gy);
-                gzd = warp_sum_d((double)gz);
-            }
         }
+        if (GRAD) gacc.reduce(gxd, gyd, gzd);
         __syncwarp();
         if (lane == 0) {
             if (S->bad) {

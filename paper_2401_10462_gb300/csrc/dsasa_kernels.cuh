@@ -44,7 +44,7 @@ enum : int {
     ST_CAND_OVF = 1,      // more overlapping neighbours than one warp's candidate table holds
     ST_TRI_OVF = 2,       // cell needed more vertex slots than available
     ST_UNRESOLVED = 4,    // exact expansion capacity exceeded
-    ST_DEGENERATE = 8,    // an exact tie (zero predicate) was met
+    ST_DEGENERATE = 8,    // a clip tie that Simulation of Simplicity cannot break (coincident atoms)
     ST_BADCELL = 16,      // inconsistent cell structure detected (atom output set to NaN)
     ST_INPUT = 32,        // non-finite input
     ST_EXPORT_OVF = 64,   // complex export buffer too small

@@ -324,6 +324,52 @@ DS_HD PlaneN<XP> xp_ghost(int g, double h) {
     return P;
 }
 
+// ------------------------------------------------------------------ Simulation of Simplicity
+// Ties of the clip test are broken as the regular triangulation breaks ties of its power
+// test (Edelsbrunner & Muecke 1990): every atom weight is perturbed, w_k -> w_k + delta_k,
+// with infinitesimal delta_k and the delta of a lower atom index dominating every delta of a
+// higher one.  With w_i -> w_i + delta_i for the centre atom, an atom plane moves by
+// b_k -> b_k + (delta_i - delta_k) / 2; a ghost plane of the initial cube does not move.  The
+// clip value P = q_M . Dv - b_M D of vertex (A, B, C) against plane M is linear in the b's:
+//     dP/db_A = q_M . (q_B x q_C),  dP/db_B = q_M . (q_C x q_A),  dP/db_C = q_M . (q_A x q_B),
+//     dP/db_M = -D,
+// so the perturbed sign of an exact zero is the sign of the coefficient of the lowest-indexed
+// atom whose coefficient is not zero: -dP/db_k / 2 for a plane atom k, and the sum of the
+// atom planes' dP/db_k / 2 for the centre atom i.  (P = -F/2 of the conflict determinant F of
+// the tetrahedron (i, A, B, C) against M, so this is the perturbation of that test.)  g[] holds
+// the global indices of A, B, C, M (negative for ghost planes) and gi that of atom i.  Returns
+// +1 (the vertex is beyond M: clipped) or -1; 0 only if every coefficient vanishes, which
+// needs coincident atoms.
+DS_HD int sos_clip_sign(const PlaneN<XP>* P, const int* g, int gi) {
+    const PlaneN<XP>& A = P[0];
+    const PlaneN<XP>& B = P[1];
+    const PlaneN<XP>& C = P[2];
+    const PlaneN<XP>& M = P[3];
+    XP dP[4];
+    dP[0] = vdot(M.q, vcross(B.q, C.q));
+    dP[1] = vdot(M.q, vcross(C.q, A.q));
+    dP[2] = vdot(M.q, vcross(A.q, B.q));
+    dP[3] = -vdot(A.q, vcross(B.q, C.q));
+    XP ci = xp_zero();
+    for (int k = 0; k < 4; ++k)
+        if (g[k] >= 0) ci = ci + dP[k];
+    // candidates in increasing index: atom i, then the plane atoms
+    int best = -1, order_idx = 0x7fffffff;
+    int done_mask = 0;
+    for (int step = 0; step < 5; ++step) {
+        best = -2;
+        order_idx = 0x7fffffff;
+        if (!(done_mask & 16) && gi < order_idx) { best = 4; order_idx = gi; }
+        for (int k = 0; k < 4; ++k)
+            if (!(done_mask & (1 << k)) && g[k] >= 0 && g[k] < order_idx) { best = k; order_idx = g[k]; }
+        if (best == -2) break;
+        done_mask |= 1 << best;
+        const int sg = best == 4 ? xp_sign(ci) : -xp_sign(dP[best]);
+        if (sg != 0) return sg;
+    }
+    return 0;
+}
+
 // ------------------------------------------------------------------ geometric terms
 template <class T> struct P3 { T x, y, z; };
 template <class T> DS_HD P3<T> operator+(P3<T> a, P3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
@@ -521,6 +567,11 @@ DS_HD FF ff_add(FF a, FF b) {
     return ff_norm(s, e + (a.l + b.l));
 }
 DS_HD FF ff_sub(FF a, FF b) { return ff_add(a, FF{-b.h, -b.l}); }
+DS_HD FF ff_add_f(FF a, float b) {   // a + b for a plain float b
+    float s, e;
+    two_sum_f(a.h, b, s, e);
+    return ff_norm(s, e + a.l);
+}
 DS_HD FF ff_mul_f(FF a, float b) {
     float p = a.h * b;
     float e = fmaf(a.h, b, -p);

@@ -109,16 +109,16 @@ class Server:
         off = slot.offsets
         ha = slot.h_area.numpy()
         hg = slot.h_grad.numpy()
-        for k, r in enumerate(slot.batch):
+        batch = slot.batch
+        for k, r in enumerate(batch):
             r.areas = ha[off[k]:off[k + 1]].copy()
             if self.with_grad:
                 r.grad = hg[off[k]:off[k + 1]].copy()
             r.status = code
-        if code != api.DSASA_OK and len(slot.batch) > 1:
+        if code != api.DSASA_OK and len(batch) > 1:
             # the status word covers the whole batch: run its requests one by one to find
-            # which of them failed (the others keep the outputs computed just now, which
-            # do not depend on the batch)
-            for r in slot.batch:
+            # which of them failed (each one's outputs do not depend on the batch)
+            for r in batch:
                 self._launch(slot, [r])
                 slot.event.synchronize()
                 r.status = slot.ctx.status_code()
@@ -126,7 +126,7 @@ class Server:
                 if self.with_grad:
                     r.grad = slot.h_grad.numpy()[: r.n].copy()
         t_now = time.perf_counter() - t0
-        for r in slot.batch:
+        for r in batch:
             r.done = t_now
         slot.batch = []
         slot.event = None

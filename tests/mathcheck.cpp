@@ -69,6 +69,20 @@ int mc_pred(int kind, int tier, const double* xyzR) {
     return xp_sign(v);
 }
 
+// clip test of vertex (A, B, C) against plane M relative to atom i (rows i, A, B, C, M) with
+// exact zeros broken by Simulation of Simplicity; g = global indices of i, A, B, C, M
+int mc_sos_clip(const double* xyzR, const int* g) {
+    const double* I = xyzR;
+    PlaneN<XP> P[4];
+    for (int k = 0; k < 4; ++k) P[k] = px(I, xyzR + 4 * (k + 1));
+    XP v = pred_clip(P[0], P[1], P[2], P[3]);
+    if (v.ovf) return 2;
+    int s = xp_sign(v);
+    if (s != 0) return s;
+    int gg[4] = {g[1], g[2], g[3], g[4]};
+    return 10 * sos_clip_sign(P, gg, g[0]);   // x10: marks a decision taken by the tie-break
+}
+
 int mc_xp_len(int kind, const double* xyzR) {
     const double* I = xyzR;
     PlaneN<XP> P[4];

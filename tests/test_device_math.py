@@ -28,6 +28,7 @@ def mc():
     dp = ctypes.POINTER(ctypes.c_double)
     lib.mc_pred.argtypes = [ctypes.c_int, ctypes.c_int, dp]
     lib.mc_xp_len.argtypes = [ctypes.c_int, dp]
+    lib.mc_sos_clip.argtypes = [dp, ctypes.POINTER(ctypes.c_int)]
     lib.mc_dihedral_grad.argtypes = [dp, dp, ctypes.c_int]
     lib.mc_dihedral_grad.restype = ctypes.c_double
     lib.mc_solid_angle.argtypes = [dp, dp, dp]
@@ -255,3 +256,31 @@ def test_signed_dihedral_gradient_and_cap(mc):
     for d, R1, R2 in ((4.0, 3.1, 2.6), (0.7, 3.2, 2.6), (5.6, 2.9, 3.0)):
         t = (d * d + R1 * R1 - R2 * R2) / (2 * d)
         assert mc.mc_cap64(d, R1, R2) == pytest.approx(2 * np.pi * R1 * (R1 - t), rel=1e-13)
+
+
+def test_clip_ties_broken_as_the_oracle_breaks_them(mc, orc):
+    """A cell vertex exactly on a bisector (lattice atoms: the vertex of the three axis
+    neighbours lies on the bisector of the body- and face-diagonal ones) is decided by the
+    device's Simulation of Simplicity exactly as the oracle's power test decides the same
+    tie, for every assignment of atom indices (which decides the perturbation's order)."""
+    import itertools
+    base = np.array([[0.0, 0.0, 0.0], [2.5, 0.0, 0.0], [0.0, 2.5, 0.0], [0.0, 0.0, 2.5]])
+    shifts = (np.array([10.0, -3.0, 7.5]), np.array([-41.5, 12.25, 0.5]))
+    ties = 0
+    for m in ([2.5, 2.5, 2.5], [2.5, 2.5, 0.0], [0.0, 2.5, 2.5]):
+        for radii in ((1.5, 1.5, 1.5, 1.5, 1.5), (1.2, 1.2, 1.2, 1.2, 1.2)):
+            for sh in shifts:
+                rows = np.zeros((5, 4))
+                rows[:4, :3] = base + sh
+                rows[4, :3] = np.array(m) + sh
+                rows[:, 3] = np.array(radii) + P
+                for perm in itertools.permutations(range(5)):
+                    g = np.array(perm, dtype=np.int32)          # global index of row k is perm[k]
+                    got = mc.mc_sos_clip(_d(rows), g.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+                    assert abs(got) == 10, got                  # an exact tie, broken by the perturbation
+                    pts = np.zeros((5, 4))
+                    pts[g] = rows                                # the oracle's point k has index k
+                    ref = orc.predicate(1, pts, [int(x) for x in g])   # -1: conflict (clipped)
+                    assert (got > 0) == (ref == -1), (m, radii, perm, got, ref)
+                    ties += 1
+    assert ties == 3 * 2 * 2 * 120

@@ -133,13 +133,13 @@ def test_too_many_neighbours_gives_capacity_and_one_nan(api, torch_cuda, orc):
 
 @pytest.mark.gpu
 def test_verlet_list_overflow_forces_rebuild(api, torch_cuda, orc):
-    """A ball with 100 overlapping neighbours and 40 more in the skin band (141 > 122 list
+    """A ball with 55 overlapping neighbours and 70 more in the skin band (125 > 122 list
     entries): its list cannot be kept, so every call rebuilds the cell list; the results are
-    still exact (the plane table holds only the 100 overlapping balls) and no error is
+    still exact (the plane table holds only the 55 overlapping balls) and no error is
     reported."""
     torch = torch_cuda
-    xyz = np.concatenate([np.full((1, 3), 1e-5), _spiral(100, 8.0, 2), _spiral(40, 10.5, 3)])
-    r = np.concatenate([[6.0], np.full(140, 1.2)])
+    xyz = np.concatenate([np.full((1, 3), 1e-5), _spiral(55, 8.0, 2), _spiral(70, 10.5, 3)])
+    r = np.concatenate([[6.0], np.full(125, 1.2)])
     x, rr = _dev(torch, xyz), _dev(torch, r)
     ctx = api.Context(skin=1.0)
     a = torch.empty(len(r), dtype=torch.float64, device="cuda")

@@ -150,6 +150,34 @@ def test_dual_complex_bit_exact(api, torch_cuda, orc, gen, case, precision):
     _check_complex(api, torch_cuda, orc, xyz, r, precision)
 
 
+def _degenerate(case):
+    if case == "lattice":
+        # 4 x 4 x 3 cubic lattice of equal balls: every cell vertex is met by several
+        # bisectors (co-spherical and co-planar atoms everywhere)
+        g = np.stack(np.meshgrid(np.arange(4), np.arange(4), np.arange(3), indexing="ij"), -1).reshape(-1, 3)
+        return g * 2.5, np.full(len(g), 1.5)
+    # eight equal balls on the corners of a cube (co-spherical) around a smaller central ball,
+    # and the six face centres one layer out
+    c = np.array([[x, y, z] for x in (-1.5, 1.5) for y in (-1.5, 1.5) for z in (-1.5, 1.5)])
+    f = np.array([[3.5, 0, 0], [-3.5, 0, 0], [0, 3.5, 0], [0, -3.5, 0], [0, 0, 3.5], [0, 0, -3.5]])
+    xyz = np.concatenate([[[0.0, 0.0, 0.0]], c, f]) + np.array([4.0, -2.0, 1.5])
+    return xyz, np.concatenate([[1.2], np.full(8, 1.5), np.full(6, 1.7)])
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("case", ["lattice", "cospherical"])
+def test_degenerate_inputs_resolved_as_the_oracle(api, torch_cuda, orc, case, precision):
+    """Exactly degenerate inputs (no jitter): the device breaks the ties of its clip test by
+    the same Simulation of Simplicity as the oracle's triangulation, so the complex is the
+    oracle's, the status is OK and the areas and gradient match."""
+    xyz, r = _degenerate(case)
+    _check_complex(api, torch_cuda, orc, xyz, r, precision)
+    a, g = gpu_sasa(api, torch_cuda, xyz, r, precision)     # raises on a non-OK status
+    ra, _, rg = orc.sasa(xyz, r)
+    check_areas(a, ra)
+    check_grad(g, rg)
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_globule_5000(api, torch_cuda, orc, gen, precision):
     m = gen.globule(5000, 0)
