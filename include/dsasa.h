@@ -66,9 +66,11 @@ typedef enum {
  *                 one float-float warp sum; the per-atom constants (multiples of 2 pi R_i^2)
  *                 are added once in FP64.  The gradient is summed in FP32.  Predicates are
  *                 filtered in FP32, then FP64, then decided by exact expansions.
- *                 Limit: an atom whose exposed area is a sliver (about 1e-5 A^2) gets its
- *                 gradient from terms that cancel about a million-fold, so its FP32 gradient
- *                 can miss a 1e-3 relative bound; DSASA_FP64 has no such limit.
+ *                 The gradient contributions of an atom are summed in float-float.  An atom
+ *                 whose FP32 contributions cancel too far (a sliver: an exposed area of about
+ *                 1e-5 A^2 from terms a million times larger) is detected on the device and
+ *                 computed again in FP64 by the large-capacity pass, which in this form runs
+ *                 in FP64 for every atom it takes (dsasa_refined_count).
  *   DSASA_FP64  - every term in FP64; predicates filtered in FP64, then exact. */
 enum { DSASA_MIXED = 0, DSASA_FP64 = 1 };
 
@@ -117,6 +119,18 @@ dsasa_status dsasa_compute_volume(dsasa_ctx* ctx, const double* coords, const do
                                   int64_t n, double* areas_out, double* grad_out, double* volumes_out,
                                   double* vol_grad_out);
 
+/* Weighted molecular-volume gradient (the vector-Jacobian product of the per-atom volumes,
+ * which reverse-mode differentiation of an energy sum_i c_i V_i needs): as
+ * dsasa_compute_volume, with vol_grad_out[j] = d(sum_i w_i V_i)/d(p_j) for volume_weights w
+ * (double[n], device; NULL means all ones, the union volume's gradient).  Moving p_j moves
+ * only the face of each neighbour's cell towards j, so dV_i/dp_j = (s q - m) / |q| with s
+ * the area and m the first moment (relative to p_i) of that face's part inside B_i,
+ * q = p_j - p_i; the face is the same polygon in j's cell.  volumes_out and vol_grad_out
+ * are required (device). */
+dsasa_status dsasa_compute_volume_vjp(dsasa_ctx* ctx, const double* coords, const double* radii, double probe,
+                                      int64_t n, const double* volume_weights, double* areas_out,
+                                      double* volumes_out, double* vol_grad_out);
+
 /* Shrake-Rupley numerical SASA, an on-device cross-check of the exact areas (no equation of
  * the paper; the numerical method of its accuracy comparison): unit_points is float[m][3]
  * (device, caller-owned) of unit vectors placed on every probe-inflated sphere; a point is
@@ -163,9 +177,18 @@ dsasa_status dsasa_compute_host(dsasa_ctx* ctx, const double* coords_host, const
 dsasa_status dsasa_status_sync(dsasa_ctx* ctx);
 
 /* Diagnostics (no paper counterpart): synchronises the stream and writes to *deferred how
- * many atoms of the most recent compute call had a cell larger than the fast pass holds
- * (64 neighbour planes or 64 cell vertices) and were finished by the large-capacity pass. */
+ * many atoms of the most recent compute call were finished by the large-capacity pass:
+ * atoms whose cell is larger than the fast pass holds (64 neighbour planes or 64 cell
+ * vertices) and, in the DSASA_MIXED form, atoms that the cancellation detector handed to
+ * that pass (it runs in FP64 there; see dsasa_refined_count). */
 dsasa_status dsasa_deferred_count(dsasa_ctx* ctx, int64_t* deferred);
+
+/* Diagnostics (no paper counterpart): synchronises the stream and writes to *refined how
+ * many atoms of the most recent DSASA_MIXED compute call had a gradient whose FP32
+ * contributions cancel too far for the FP32 form (their summed magnitudes times 2^-20 above a
+ * quarter of the gradient tolerance scale 1e-3 max(|g|, 1e-2)): those atoms' outputs were
+ * computed again in FP64 by the large-capacity pass. */
+dsasa_status dsasa_refined_count(dsasa_ctx* ctx, int64_t* refined);
 
 /* Per-kernel timing (diagnostics, no paper counterpart).  With timing enabled, each compute
  * call records CUDA events on the context's stream around its kernels; dsasa_kernel_times

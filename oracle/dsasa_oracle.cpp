@@ -933,8 +933,65 @@ static double tri_disk_area(double ax, double ay, double bx, double by, double r
     return sector(ax, ay, bx, by);
 }
 
+// First moment (integral of the position, 2-D) of the same signed region as tri_disk_area:
+// the part of the triangle (0, a, b) inside the disk |x| <= r.  A straight piece (0, u, v)
+// contributes its signed area times its centroid (u + v) / 3; a circular sector from u to v
+// (|u| = |v| = r) contributes r^2 / 3 times (v - u) turned by -90 degrees, the integral of
+// r^3 (cos t, sin t) / 3 over its angle.
+static void tri_disk_moment(double ax, double ay, double bx, double by, double r, double& mx, double& my) {
+    auto cross = [](double ux, double uy, double vx, double vy) { return ux * vy - uy * vx; };
+    mx = my = 0.0;
+    auto tri = [&](double ux, double uy, double vx, double vy) {
+        const double w = 0.5 * cross(ux, uy, vx, vy) / 3.0;
+        mx += w * (ux + vx);
+        my += w * (uy + vy);
+    };
+    auto sector = [&](double ux, double uy, double vx, double vy) {
+        mx += r * r / 3.0 * (vy - uy);
+        my += r * r / 3.0 * (ux - vx);
+    };
+    const double r2 = r * r;
+    const double aa = ax * ax + ay * ay, bb = bx * bx + by * by;
+    const bool ain = aa <= r2, bin = bb <= r2;
+    if (ain && bin) { tri(ax, ay, bx, by); return; }
+    const double dx = bx - ax, dy = by - ay;
+    const double A = dx * dx + dy * dy, B = ax * dx + ay * dy, C = aa - r2;
+    const double disc = B * B - A * C;
+    if (ain) {
+        double t1 = (-B + std::sqrt(std::max(disc, 0.0))) / A;
+        double px = ax + t1 * dx, py = ay + t1 * dy;
+        tri(ax, ay, px, py);
+        sector(px, py, bx, by);
+        return;
+    }
+    if (bin) {
+        double t0 = (-B - std::sqrt(std::max(disc, 0.0))) / A;
+        double px = ax + t0 * dx, py = ay + t0 * dy;
+        sector(ax, ay, px, py);
+        tri(px, py, bx, by);
+        return;
+    }
+    if (A > 0 && disc > 0) {
+        double sq = std::sqrt(disc), t0 = (-B - sq) / A, t1 = (-B + sq) / A;
+        if (t0 > 0 && t1 < 1) {
+            double px = ax + t0 * dx, py = ay + t0 * dy, qx = ax + t1 * dx, qy = ay + t1 * dy;
+            sector(ax, ay, px, py);
+            tri(px, py, qx, qy);
+            sector(qx, qy, bx, by);
+            return;
+        }
+    }
+    sector(ax, ay, bx, by);
+}
+
+// Volumes V_i = vol(B_i cap L_i) and, with weights w (NULL = ones), the gradient
+// d(sum_i w_i V_i)/dp.  Moving p_j moves only the face of L_i towards j, so
+// dV_i/dp_j = s (p_j - C) / |p_j - p_i| with s the area and C the centroid of that face's part
+// inside B_i (the same polygon for cell j: on the bisector the two balls have equal power);
+// dV_i/dp_i = -sum_j dV_i/dp_j (translation).  In the frame of atom k the gradient entry is
+//   g_k = sum_faces [(w_k - w_j) m - w_k s q] / |q|,  q = p_j - p_k, m = s (C - p_k).
 static void compute_volumes(const Result& res, const std::vector<long double>& A, std::vector<double>& vol,
-                            std::vector<double>& grad) {
+                            std::vector<double>& grad, const double* w = nullptr) {
     const Geo& g = res.g;
     const int n = res.n;
     vol.assign(n, 0.0);
@@ -1011,16 +1068,24 @@ static void compute_volumes(const Result& res, const std::vector<long double>& A
                 V3 d = {z[0] - c[0], z[1] - c[1], z[2] - c[2]};
                 poly.push_back({dotv(d, e1), dotv(d, e2)});
             }
-            double area = 0.0;
+            double area = 0.0, m1 = 0.0, m2 = 0.0;
             const double r = std::sqrt(rho2);
             for (size_t k = 0; k < poly.size(); ++k) {
                 const auto& P0 = poly[k];
                 const auto& P1 = poly[(k + 1) % poly.size()];
                 area += tri_disk_area(P0[0], P0[1], P1[0], P1[1], r);
+                double mx, my;
+                tri_disk_moment(P0[0], P0[1], P1[0], P1[1], r, mx, my);
+                m1 += mx;
+                m2 += my;
             }
-            area = std::fabs(area);
+            if (area < 0) { area = -area; m1 = -m1; m2 = -m2; }   // the ring's orientation
             vol[own] += h * area / 3.0;
-            for (int k = 0; k < 3; ++k) grad[3 * own + k] -= area * u[k];
+            const double wo = w ? w[own] : 1.0, wt = w ? w[oth] : 1.0;
+            // first moment of the in-ball face part relative to p_own: area c + in-plane part
+            const double mom[3] = {area * c[0] + m1 * e1.x + m2 * e2.x, area * c[1] + m1 * e1.y + m2 * e2.y,
+                                   area * c[2] + m1 * e1.z + m2 * e2.z};
+            for (int k = 0; k < 3; ++k) grad[3 * own + k] += ((wo - wt) * mom[k] - wo * area * q[k]) / qn;
         }
     }
     for (int i = 0; i < n; ++i) vol[i] += g.pts[i].R * (double)A[i] / 3.0;
@@ -1110,12 +1175,13 @@ long oracle_areas_parallel(const OracleHandle* h, const double* weights, double*
     return a.n_tri_bad;
 }
 
-// per-atom volumes vol(B_i cap L_i) [n], d vol(union)/dx [3n] (may be NULL), total volume
-long oracle_volumes(const OracleHandle* h, double* volumes, double* grad, double* total) {
+// per-atom volumes vol(B_i cap L_i) [n], d(sum_i w_i V_i)/dx [3n] (may be NULL; weights NULL
+// = ones: the gradient of the union volume), total volume
+long oracle_volumes(const OracleHandle* h, const double* weights, double* volumes, double* grad, double* total) {
     Areas a;
     compute_areas(h->res, nullptr, false, a);
     std::vector<double> v, g;
-    compute_volumes(h->res, a.A, v, g);
+    compute_volumes(h->res, a.A, v, g, weights);
     long double tot = 0;
     for (int i = 0; i < h->res.n; ++i) { volumes[i] = v[i]; tot += v[i]; }
     if (total) *total = (double)tot;

@@ -63,7 +63,7 @@ def _load():
             lib.oracle_areas.restype = ctypes.c_long
             lib.oracle_areas_parallel.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, ctypes.c_int, ip]
             lib.oracle_areas_parallel.restype = ctypes.c_long
-            lib.oracle_volumes.argtypes = [ctypes.c_void_p, dp, dp, dp]
+            lib.oracle_volumes.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
             lib.oracle_volumes.restype = ctypes.c_long
             lib.oracle_gauss_bonnet.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
             lib.oracle_gauss_bonnet.restype = ctypes.c_int
@@ -165,13 +165,16 @@ class Oracle:
             raise RuntimeError(f"{bad} triangles of C without a triple point")
         return a[: self.n], tot.value, (g[: self.n] if g is not None else None), used.value
 
-    def volumes(self, grad: bool = True):
+    def volumes(self, grad: bool = True, weights=None):
         """Per-atom volumes vol(B_i cap L_i), their total (the union volume) and
-        d(total)/dx (n, 3) (None if grad=False)."""
+        d(sum_i w_i V_i)/dx (n, 3) (None if grad=False; weights None = ones, the gradient of
+        the union volume)."""
         v = np.zeros(max(self.n, 1))
         g = np.zeros((max(self.n, 1), 3)) if grad else None
         tot = ctypes.c_double(0)
-        bad = self._lib.oracle_volumes(self._h, _d(v), _d(g) if g is not None else None, ctypes.byref(tot))
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64).reshape(-1)
+        bad = self._lib.oracle_volumes(self._h, _d(w) if w is not None else None, _d(v),
+                                       _d(g) if g is not None else None, ctypes.byref(tot))
         if bad:
             raise RuntimeError(f"{bad} triangles of C without a triple point")
         return v[: self.n], tot.value, (g[: self.n] if g is not None else None)

@@ -42,6 +42,7 @@ _lib.dsasa_set_precision.argtypes = [_vp, ctypes.c_int]
 _lib.dsasa_compute.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp]
 _lib.dsasa_compute_vjp.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp, _vp]
 _lib.dsasa_compute_volume.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp, _vp, _vp]
+_lib.dsasa_compute_volume_vjp.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp, _vp, _vp]
 _lib.dsasa_compute_sr.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, ctypes.c_int, _vp, _vp]
 _lib.dsasa_sr_tests.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_lists_reused.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
@@ -50,6 +51,7 @@ _lib.dsasa_compute_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_
 _lib.dsasa_compute_host.argtypes = [_vp, _dp, _dp, ctypes.c_double, _i64, _dp, _dp, _dp]
 _lib.dsasa_status_sync.argtypes = [_vp]
 _lib.dsasa_deferred_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+_lib.dsasa_refined_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_set_timing.argtypes = [_vp, ctypes.c_int]
 _lib.dsasa_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_export_complex.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_int64)]
@@ -62,14 +64,16 @@ _lib.dsasa_destroy.argtypes = [_vp]
 _lib.dsasa_version.restype = ctypes.c_char_p
 for _f in ("dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute", "dsasa_compute_vjp",
            "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync", "dsasa_export_complex",
-           "dsasa_deferred_count", "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume", "dsasa_compute_sr",
+           "dsasa_deferred_count", "dsasa_refined_count", "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume",
+           "dsasa_compute_volume_vjp", "dsasa_compute_sr",
            "dsasa_sr_tests", "dsasa_lists_reused"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 EXPORTED = ("dsasa_default_config", "dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute",
             "dsasa_compute_vjp", "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync",
             "dsasa_export_complex", "dsasa_last_error", "dsasa_destroy", "dsasa_version", "dsasa_deferred_count",
-            "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume",
+            "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume", "dsasa_refined_count",
+            "dsasa_compute_volume_vjp",
             "dsasa_compute_sr", "dsasa_sr_tests", "dsasa_lists_reused", "dsasa_kernel_launches",
             "dsasa_debug_fail_allocations")
 
@@ -177,6 +181,22 @@ class Context:
         self._raise(_lib.dsasa_compute_volume(self._h, _ptr(coords), _ptr(radii), float(probe), n, _ptr(areas_out),
                                               _ptr(grad_out), _ptr(volumes_out), _ptr(vol_grad_out)))
 
+    def compute_volume_vjp(self, coords, radii, weights, areas_out, volumes_out, vol_grad_out,
+                           probe: float = PROBE):
+        """dsasa_compute_volume_vjp: areas, per-atom volumes and d(sum_i w_i V_i)/dx for volume
+        weights w (device tensor, or None for ones)."""
+        n = int(coords.shape[0])
+        _check_tensor(coords, "coords", n, 3)
+        _check_tensor(radii, "radii", n)
+        _check_tensor(areas_out, "areas_out", n)
+        _check_tensor(volumes_out, "volumes_out", n)
+        _check_tensor(vol_grad_out, "vol_grad_out", n, 3)
+        if weights is not None:
+            _check_tensor(weights, "weights", n)
+        self._sync_stream()
+        self._raise(_lib.dsasa_compute_volume_vjp(self._h, _ptr(coords), _ptr(radii), float(probe), n, _ptr(weights),
+                                                  _ptr(areas_out), _ptr(volumes_out), _ptr(vol_grad_out)))
+
     def compute_sr(self, coords, radii, unit_points, areas_out, exposed_out=None, probe: float = PROBE):
         """dsasa_compute_sr: Shrake-Rupley areas on the m float32 unit vectors unit_points
         (device tensor (m, 3)); optional int32 exposed-point counts."""
@@ -254,6 +274,12 @@ class Context:
         """Atoms of the last call whose cell went to the large-capacity pass."""
         d = ctypes.c_int64(0)
         self._raise(_lib.dsasa_deferred_count(self._h, ctypes.byref(d)))
+        return int(d.value)
+
+    def refined_count(self) -> int:
+        """Atoms of the last mixed-form call recomputed in FP64 (cancellation detector)."""
+        d = ctypes.c_int64(0)
+        self._raise(_lib.dsasa_refined_count(self._h, ctypes.byref(d)))
         return int(d.value)
 
     def status_code(self) -> int:

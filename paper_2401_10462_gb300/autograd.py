@@ -7,6 +7,9 @@
 * ``sasa_areas(coords, radii)`` returns the per-atom areas A_i; its backward receives
   dL/dA and recomputes the cells with those weights (a vector-Jacobian product) instead of
   storing per-simplex intermediates.
+* ``molecular_volumes(coords, radii)`` returns the per-atom volumes V_i (sum = the solvent-
+  accessible volume); its backward recomputes the cells with dL/dV as volume weights
+  (dsasa_compute_volume_vjp).
 * ``GraphedTrajectory`` captures one trajectory step (a Gaussian displacement of every
   atom, E_np and its gradient through autograd) in a CUDA graph with fixed capacities; the
   device status word is checked after replays.
@@ -70,6 +73,40 @@ class SASAAreas(torch.autograd.Function):
         # recompute the cells with the incoming weights: grad = d(sum_i g_i A_i)/dx
         ctx.lib_ctx.compute(coords, radii.contiguous(), areas, grad, weights=g_areas.contiguous(), probe=ctx.probe)
         return grad, None, None, None
+
+
+class MolecularVolumes(torch.autograd.Function):
+    """Per-atom volumes V_i = vol(B_i cap L_i) (their sum is the solvent-accessible volume);
+    backward recomputes the cells with the incoming weights (dsasa_compute_volume_vjp)."""
+
+    @staticmethod
+    def forward(ctx, coords, radii, probe, lib_ctx):
+        n = coords.shape[0]
+        areas = torch.empty(n, dtype=torch.float64, device=coords.device)
+        vols = torch.empty(n, dtype=torch.float64, device=coords.device)
+        lib_ctx.compute_volume(coords.detach().contiguous(), radii.contiguous(), areas, vols, probe=probe)
+        ctx.save_for_backward(coords.detach(), radii)
+        ctx.probe = probe
+        ctx.lib_ctx = lib_ctx
+        return vols
+
+    @staticmethod
+    def backward(ctx, g_vols):
+        coords, radii = ctx.saved_tensors
+        n = coords.shape[0]
+        areas = torch.empty(n, dtype=torch.float64, device=coords.device)
+        vols = torch.empty(n, dtype=torch.float64, device=coords.device)
+        grad = torch.empty((n, 3), dtype=torch.float64, device=coords.device)
+        ctx.lib_ctx.compute_volume_vjp(coords, radii.contiguous(), g_vols.contiguous(), areas, vols, grad,
+                                       probe=ctx.probe)
+        return grad, None, None, None
+
+
+def molecular_volumes(coords, radii, probe: float = api.PROBE, precision: str = "mixed", lib_ctx=None):
+    """Per-atom volumes of the union of probe-inflated balls, differentiable in coords."""
+    if lib_ctx is None:
+        lib_ctx = _Ctxs.get(coords.device.index or 0, precision)
+    return MolecularVolumes.apply(coords, radii, probe, lib_ctx)
 
 
 def nonpolar_energy(coords, radii, gamma=GAMMA, probe: float = api.PROBE, precision: str = "mixed", lib_ctx=None):

@@ -102,6 +102,19 @@ using CellRecF = CellRec<float, 64, 64>;
 using CellRecD = CellRec<double, 64, 64>;
 static_assert(offsetof(CellRecF, iK) % 16 == 0 && offsetof(CellRecD, iK) % 16 == 0,
               "the record header (iK, icl, nc, hw) is read as one 16-byte load");
+// The plane rows move in 16-byte pieces (copy_row, load_row, store_row): every row of the
+// shared table and of a record must start on a 16-byte boundary.  Records are indexed as an
+// array of CellRec (and the per-warp tables as an array of Smem), so their sizes must keep
+// the next element's rows aligned too.
+template <class R, int NE, int NT> constexpr bool rows_aligned() {
+    using SM = Smem<R, NE, NT>;
+    using RC = CellRec<R, NE, NT>;
+    return offsetof(SM, pq) % 16 == 0 && sizeof(R[4]) % 16 == 0 && sizeof(SM) % 16 == 0 &&
+           offsetof(RC, pq) % 16 == 0 && sizeof(RC) % 16 == 0 && alignof(SM) >= 16 && alignof(RC) >= 16;
+}
+static_assert(rows_aligned<float, 64, 64>() && rows_aligned<double, 64, 64>() && rows_aligned<float, 128, 128>() &&
+                  rows_aligned<double, 128, 128>(),
+              "16-byte plane-row moves need 16-byte aligned rows in every table and record");
 
 // one plane row (4 values of R) between the shared table and a cell record, 16-byte moves
 template <class R> __device__ __forceinline__ void copy_row(R* dst, const R* src) {
@@ -158,10 +171,12 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 template <class R> struct GAcc;
 template <> struct GAcc<float> {
     FF x{0.f, 0.f}, y{0.f, 0.f}, z{0.f, 0.f};
+    float mag = 0.f;   // sum of |contribution| over the components (the cancellation detector)
     __device__ __forceinline__ void add(float a, float b, float c) {
         x = ff_add_f(x, a);
         y = ff_add_f(y, b);
         z = ff_add_f(z, c);
+        mag += fabsf(a) + fabsf(b) + fabsf(c);
     }
     // warp sum (every lane ends with the same value: the float-float sum is commutative)
     __device__ __forceinline__ void reduce(double& gx, double& gy, double& gz) {
@@ -184,6 +199,15 @@ template <> struct GAcc<double> {
         gz = warp_sum_d(z);
     }
 };
+// Cancellation detector of the FP32 form.  An FP32 gradient contribution c carries an error
+// of at most about REFINE_EPS |c| (its geometry, square roots and atan2 in float); the
+// float-float sum adds none of its own.  When REFINE_EPS times the summed magnitudes of an
+// atom's contributions could exceed REFINE_TOL of the gradient tolerance scale
+// max(|g|, 1e-2) (a quarter of the stated 1e-3), the atom is handed to the FP64 pass, whose
+// outputs replace the FP32 ones: such atoms are the slivers whose exposed area and gradient
+// come from terms that cancel many orders of magnitude.
+constexpr float REFINE_EPS = 9.5367431640625e-07f;   // 2^-20 = 16 float ulps of 2^-24
+constexpr double REFINE_TOL = 2.5e-4;
 __device__ __forceinline__ uint8_t tv_get(const uchar4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 template <class SM> __device__ __forceinline__ void ta_set(SM* S, int t, int k, uint8_t s) {
     ((uint8_t*)&S->ta[t & (SM::kNT - 1)])[k] = s;
@@ -300,11 +324,17 @@ template <class SM, class R = typename SM::Real> __device__ __noinline__ VtxFA<R
 // closed surface of B_i cap L_i:  V_i = (R_i A_i + sum_f h_f s_f) / 3.  The exposed sphere
 // piece has vector area -sum_f s_f u_f = d vol(union) / d p_i; since the whole cell's faces
 // have zero vector area, that is +sum_f o_f u_f, which vanishes exactly (no cancellation)
-// when the cell lies inside the ball.  Per lane: partial sums over faces.
+// when the cell lies inside the ball.  With volume weights (vw != NULL) the gradient of
+// sum_i w_i V_i also needs, for every face towards an atom k, the first moment m_f of its part
+// inside the ball (relative to p_i): moving p_k moves only that face, by
+// dV_i/dp_k = (s_f q_k - m_f) / |q_k|, and the face is the same polygon in k's cell; the
+// weighted entry is w_i (the unweighted one) + sum_f (w_i - w_k) m_f / |q_f| (wx, wy, wz).
+// Per lane: partial sums over faces.
 template <class SM, class R = typename SM::Real>
-__device__ void cell_volume_terms(const SM* S, int nc, R Ri, int lane, R& hs, R& nx, R& ny, R& nz) {
+__device__ void cell_volume_terms(const SM* S, int nc, R Ri, int lane, const double* vw, R wi, R& hs, R& nx,
+                                  R& ny, R& nz, R& wx, R& wy, R& wz) {
     constexpr int NT = SM::kNT, NE = SM::kNE;
-    hs = nx = ny = nz = (R)0;
+    hs = nx = ny = nz = wx = wy = wz = (R)0;
     for (int a = lane; a < NG + nc; a += 32) {
         const int st0 = S->start[a];
         if (st0 == NONE) continue;
@@ -324,7 +354,9 @@ __device__ void cell_volume_terms(const SM* S, int nc, R Ri, int lane, R& hs, R&
         e1 = e1 * ((R)1 / norm3(e1));
         const P3<R> e2 = cross3(u, e1);
         int t = st;
-        R fx = 0, fy = 0, px = 0, py = 0, sin_ = 0, sout = 0;
+        R fx = 0, fy = 0, px = 0, py = 0, sin_ = 0, sout = 0, m1 = 0, m2 = 0;
+        const int gk = S->pg[a];
+        const bool moments = vw != nullptr && gk >= 0 && r > (R)0;
         auto fan = [&](R ax, R ay, R bx, R by) {
             const R full = (R)0.5 * (ax * by - ay * bx);
             if (r > (R)0 && ax * ax + ay * ay <= rho2 && bx * bx + by * by <= rho2) {
@@ -333,6 +365,11 @@ __device__ void cell_volume_terms(const SM* S, int nc, R Ri, int lane, R& hs, R&
                 const R in = r > (R)0 ? tri_disk_area_ol(ax, ay, bx, by, r) : (R)0;
                 sin_ += in;
                 sout += full - in;
+            }
+            if (moments) {
+                const T2<R> mm = tri_disk_moment_ol(ax, ay, bx, by, r);
+                m1 += mm.x;
+                m2 += mm.y;
             }
         };
         for (int step = 0; step < NT; ++step) {
@@ -360,6 +397,13 @@ __device__ void cell_volume_terms(const SM* S, int nc, R Ri, int lane, R& hs, R&
         nx += sout * sg * u.x;
         ny += sout * sg * u.y;
         nz += sout * sg * u.z;
+        if (moments) {
+            // m_f = s_f (h u) + m1 e1 + m2 e2, scaled by (w_i - w_k) / |q_f|
+            const R f = (wi - (R)vw[gk]) * inv * sg;
+            wx += f * (sin_ * h * u.x + m1 * e1.x + m2 * e2.x);
+            wy += f * (sin_ * h * u.y + m1 * e1.y + m2 * e2.y);
+            wz += f * (sin_ * h * u.z + m1 * e1.z + m2 * e2.z);
+        }
     }
 }
 
@@ -467,15 +511,19 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 for (int k = 0; k < 4; ++k) Va[r][k] = q.a[k];
         };
 
-        // molecular volume of the atom from its classified cell (lane 0 writes)
+        // molecular volume of the atom from its classified cell (lane 0 writes); the gradient
+        // entry of sum_k w_k V_k (w = ones without volume weights)
         auto write_volume = [&](double Ai) {
-            R hs, nx, ny, nz;
-            cell_volume_terms(S, nc, Rr, lane, hs, nx, ny, nz);
+            R hs, nx, ny, nz, wx, wy, wz;
+            const double wv = A.vw ? A.vw[i] : 1.0;
+            cell_volume_terms(S, nc, Rr, lane, A.vgrad ? A.vw : nullptr, (R)wv, hs, nx, ny, nz, wx, wy, wz);
             const double hsum = warp_sum_d((double)hs);
             const double gx = warp_sum_d((double)nx), gy = warp_sum_d((double)ny), gz = warp_sum_d((double)nz);
+            double ex = 0.0, ey = 0.0, ez = 0.0;
+            if (A.vgrad && A.vw) { ex = warp_sum_d((double)wx); ey = warp_sum_d((double)wy); ez = warp_sum_d((double)wz); }
             if (lane == 0) {
                 A.vol[i] = (c.Ri * Ai + hsum) / 3.0;
-                if (A.vgrad) { A.vgrad[3 * i] = gx; A.vgrad[3 * i + 1] = gy; A.vgrad[3 * i + 2] = gz; }
+                if (A.vgrad) { A.vgrad[3 * i] = wv * gx + ex; A.vgrad[3 * i + 1] = wv * gy + ey; A.vgrad[3 * i + 2] = wv * gz + ez; }
             }
         };
 
@@ -1447,6 +1495,19 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             area_acc = warp_sum_d(area_acc);
         }
         if (GRAD) gacc.reduce(gxd, gyd, gzd);
+        if constexpr (FFM && GRAD) {
+            // the FP32 gradient may be too cancellation-prone for this atom: the FP64 pass that
+            // follows (the large-capacity pass) recomputes it; this pass's outputs are replaced
+            if (can_defer) {
+                float mag = gacc.mag;
+                for (int o = 16; o > 0; o >>= 1) mag += __shfl_xor_sync(FULL, mag, o);
+                const double gn = sqrt(gxd * gxd + gyd * gyd + gzd * gzd);
+                if (iK && (double)mag * (double)REFINE_EPS > REFINE_TOL * fmax(gn, 1e-2) && lane == 0) {
+                    A.defer_list[atomicAdd(A.defer_count, 1)] = s;
+                    if (A.refine_count) atomicAdd(A.refine_count, 1);
+                }
+            }
+        }
         __syncwarp();
         if (lane == 0) {
             if (S->bad) {
@@ -1580,8 +1641,16 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
         mark(2);
     }
     if (a.defer_list) {
-        if (g) go(k_atoms<R, true, 128, 128, PH_ALL>, big_blocks, WARPS * 32, big);
-        else go(k_atoms<R, false, 128, 128, PH_ALL>, big_blocks, WARPS * 32, big);
+        if constexpr (sizeof(R) == 4) {
+            // mixed form: the deferred atoms (cells beyond the fast pass's capacity, and atoms
+            // whose FP32 gradient the detector flagged) are computed by the FP64 pass
+            cudaError_t e = launch_large_f64(big, g, big_blocks, s);
+            if (err == cudaSuccess) err = e;
+            note_launches(1);
+        } else {
+            if (g) go(k_atoms<R, true, 128, 128, PH_ALL>, big_blocks, WARPS * 32, big);
+            else go(k_atoms<R, false, 128, 128, PH_ALL>, big_blocks, WARPS * 32, big);
+        }
     }
     mark(3);
     return err != cudaSuccess ? err : cudaGetLastError();

@@ -71,7 +71,7 @@ struct dsasa_ctx {
     int* vstate = nullptr;        // [0] max displacement^2 (float bits), [1] radii changed, [2] reuse, [3] overflow
     int64_t lists_n = 0;          // the lists hold this many atoms of the last single-molecule call
     double lists_probe = -1.0;
-    int* status = nullptr;      // [0] status bits, [1] total cells, [2] deferred count
+    int* status = nullptr;      // [0] status bits, [1] total cells, [2] deferred count, [3] refined count
     // optional per-kernel timing: events of up to kTimingRing calls since the last read
     bool timing = false;
     int n_timed = 0;
@@ -186,7 +186,7 @@ cudaError_t build_cells(dsasa_ctx* c, const double* coords, const double* radii,
 
 dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n, int n_mol,
                  const long long* offsets_dev, const double* w, double* areas, double* grad, int* rec,
-                 int64_t max_rec, double* vol = nullptr, double* vgrad = nullptr) {
+                 int64_t max_rec, double* vol = nullptr, double* vgrad = nullptr, const double* vw = nullptr) {
     dsasa_status st = ensure(c, n, n_mol);
     if (st != DSASA_OK) return st;
     cudaEvent_t* ev = (c->timing && c->n_timed < kTimingRing) ? c->ev[c->n_timed++] : nullptr;
@@ -219,6 +219,7 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     a.grad = grad;
     a.vol = vol;
     a.vgrad = vol ? vgrad : nullptr;
+    a.vw = vol ? vw : nullptr;
     a.n = (int)n;
     a.status = c->status;
     a.rec = rec;
@@ -226,6 +227,7 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     a.nrec = c->nrec;
     a.defer_list = c->defer;
     a.defer_count = c->status + 2;
+    a.refine_count = c->status + 3;
     a.cells = c->cells;
     a.ev = ev ? ev + 2 : nullptr;
     if (lists) {
@@ -337,6 +339,16 @@ dsasa_status dsasa_compute_volume(dsasa_ctx* c, const double* coords, const doub
     if (!volumes_out) return fail(c, DSASA_ERR_ARG, "volumes_out is NULL");
     return run(c, coords, radii, probe, n, 1, nullptr, nullptr, areas_out, grad_out, nullptr, 0, volumes_out,
                vol_grad_out);
+}
+
+dsasa_status dsasa_compute_volume_vjp(dsasa_ctx* c, const double* coords, const double* radii, double probe,
+                                      int64_t n, const double* volume_weights, double* areas_out, double* volumes_out,
+                                      double* vol_grad_out) {
+    dsasa_status st = check_common(c, coords, radii, probe, n, areas_out);
+    if (st != DSASA_OK || n == 0) return st;
+    if (!volumes_out || !vol_grad_out) return fail(c, DSASA_ERR_ARG, "volumes_out and vol_grad_out are required");
+    return run(c, coords, radii, probe, n, 1, nullptr, nullptr, areas_out, nullptr, nullptr, 0, volumes_out,
+               vol_grad_out, volume_weights);
 }
 
 dsasa_status dsasa_compute_sr(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
@@ -476,6 +488,17 @@ dsasa_status dsasa_deferred_count(dsasa_ctx* c, int64_t* deferred) {
     if (e == cudaSuccess) e = cudaMemcpy(h, c->status, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "deferred count read");
     *deferred = h[2];
+    return DSASA_OK;
+}
+
+dsasa_status dsasa_refined_count(dsasa_ctx* c, int64_t* refined) {
+    if (!c || !refined) return DSASA_ERR_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    int h[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, c->status, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "refined count read");
+    *refined = h[3];
     return DSASA_OK;
 }
 

@@ -24,7 +24,7 @@ __device__ __forceinline__ float fdec(unsigned u) {
 
 __global__ void k_bbox_init(unsigned* bbox, int n_mol, int* zero_word) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m == 0 && zero_word) *zero_word = 0;
+    if (m == 0 && zero_word) { zero_word[0] = 0; zero_word[1] = 0; }
     if (m >= n_mol) return;
     unsigned lo = fenc(INFINITY), hi = fenc(-INFINITY);
     for (int k = 0; k < 3; ++k) { bbox[8 * m + k] = lo; bbox[8 * m + 3 + k] = hi; }
@@ -272,7 +272,7 @@ __device__ __forceinline__ unsigned box_init(int k) {
     return k < 3 ? fenc(INFINITY) : (k < 6 ? fenc(-INFINITY) : (k == 6 ? fenc(0.0f) : 0u));
 }
 __global__ void __launch_bounds__(kSmallT) k_build_small(BuildArgs a) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && a.zero_word) *a.zero_word = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.zero_word) { a.zero_word[0] = 0; a.zero_word[1] = 0; }
     grid_dep_trigger();
     if (a.skip && *a.skip) return;
     __shared__ unsigned bb[8];

@@ -71,7 +71,8 @@ struct BuildArgs {
     const long long* offsets;   // device, n_mol + 1 (NULL: one molecule)
     double skin;
     const int* skip;   // non-NULL and *skip != 0: the previous cell list is reused (nothing to do)
-    int* zero_word;    // non-NULL: set to 0 by the build's first kernel (the next atom kernels' deferred count)
+    int* zero_word;    // non-NULL: zero_word[0..1] set to 0 by the build's first kernel (the next atom
+                       // kernels' deferred count and refined count)
     int max_cells;
     // outputs / scratch
     double* R;         // n
@@ -105,7 +106,8 @@ struct AtomArgs {
     double* areas;
     double* grad;           // NULL = no gradient
     double* vol;            // per-atom volumes vol(B_i cap L_i); NULL = not computed
-    double* vgrad;          // d vol(union) / dx (n x 3); NULL = not computed
+    double* vgrad;          // d(sum_i vw_i V_i) / dx (n x 3); NULL = not computed
+    const double* vw;       // volume weights vw (n); NULL = ones (the union volume's gradient)
     int n;
     int* status;
     // complex export (NULL = off): records {i, v0, v1, v2, v3}
@@ -116,6 +118,8 @@ struct AtomArgs {
     // large pass reads work_list[0 .. *work_count)
     int* defer_list;
     int* defer_count;       // zero when the first atom kernel starts (cleared by the cell-list build)
+    int* refine_count;      // NULL or the number of atoms the mixed form's detector handed to the
+                            // FP64 pass (zero at the start, cleared with defer_count)
     const int* work_list;
     const int* work_count;
     // per-atom cell records (by sorted position) between the cell kernel and the terms
@@ -166,6 +170,8 @@ cudaError_t launch_verlet_check(const double* xyz, const double* radii, const do
 cudaError_t launch_sr(const SRArgs& a, cudaStream_t s);
 cudaError_t launch_atoms_f32(const AtomArgs& a, bool grad, cudaStream_t s);
 cudaError_t launch_atoms_f64(const AtomArgs& a, bool grad, cudaStream_t s);
+// FP64 large-capacity pass over big.work_list[0 .. *big.work_count) (the mixed form's last kernel)
+cudaError_t launch_large_f64(const AtomArgs& big, bool grad, int blocks, cudaStream_t s);
 size_t scan_scratch_ints(int max_cells);
 size_t cell_record_bytes();
 

@@ -635,6 +635,60 @@ template <class T> DS_HD T tri_disk_area(T ax, T ay, T bx, T by, T r) {
     return sector(ax, ay, bx, by);
 }
 
+// First moment (the integral of the position) of the region tri_disk_area measures, in the
+// same 2-D coordinates: a straight piece (0, u, v) contributes its signed area times its
+// centroid (u + v) / 3; a circular sector from u to v on the circle |x| = r contributes
+// (r^2 / 3) (v_y - u_y, u_x - v_x), i.e. r^3 / 3 times the integral of the unit vector over
+// its angle.
+template <class T> DS_HD void tri_disk_moment(T ax, T ay, T bx, T by, T r, T& mx, T& my) {
+    const T r2 = r * r;
+    const T aa = ax * ax + ay * ay, bb = bx * bx + by * by;
+    T sx = (T)0, sy = (T)0;
+    auto piece = [&](T ux, T uy, T vx, T vy) {
+        const T w = (ux * vy - uy * vx) * (T)(1.0 / 6.0);
+        sx += w * (ux + vx);
+        sy += w * (uy + vy);
+    };
+    auto arc = [&](T ux, T uy, T vx, T vy) {
+        sx += r2 * (T)(1.0 / 3.0) * (vy - uy);
+        sy += r2 * (T)(1.0 / 3.0) * (ux - vx);
+    };
+    if (aa <= r2 && bb <= r2) {
+        piece(ax, ay, bx, by);
+    } else {
+        const T dx = bx - ax, dy = by - ay;
+        const T qa = dx * dx + dy * dy, qb = ax * dx + ay * dy, qc = aa - r2;
+        const T disc = qb * qb - qa * qc;
+        const T sq = disc > (T)0 ? ds_sqrt(disc) : (T)0;
+        if (aa <= r2) {
+            const T t1 = (-qb + sq) / qa;
+            const T px = ax + t1 * dx, py = ay + t1 * dy;
+            piece(ax, ay, px, py);
+            arc(px, py, bx, by);
+        } else if (bb <= r2) {
+            const T t0 = (-qb - sq) / qa;
+            const T px = ax + t0 * dx, py = ay + t0 * dy;
+            arc(ax, ay, px, py);
+            piece(px, py, bx, by);
+        } else {
+            bool crossed = false;
+            if (qa > (T)0 && disc > (T)0) {
+                const T t0 = (-qb - sq) / qa, t1 = (-qb + sq) / qa;
+                if (t0 > (T)0 && t1 < (T)1) {
+                    const T px = ax + t0 * dx, py = ay + t0 * dy, qx = ax + t1 * dx, qy = ay + t1 * dy;
+                    arc(ax, ay, px, py);
+                    piece(px, py, qx, qy);
+                    arc(qx, qy, bx, by);
+                    crossed = true;
+                }
+            }
+            if (!crossed) arc(ax, ay, bx, by);
+        }
+    }
+    mx = sx;
+    my = sy;
+}
+
 // ------------------------------------------------------------------ out-of-line forms
 // The kernels call the heavy terms through these (one copy of each body instead of one per
 // call site), which keeps the kernels small enough for the instruction cache.  Results are
@@ -661,6 +715,12 @@ static DS_HDC FF tri_term_ff_ol(P3<float> p2, P3<float> p3, FF R1, FF R2, FF R3,
     return tri_term_ff(p2, p3, R1, R2, R3, R1sq);
 }
 template <class T> DS_HDC T tri_disk_area_ol(T ax, T ay, T bx, T by, T r) { return tri_disk_area(ax, ay, bx, by, r); }
+template <class T> struct T2 { T x, y; };
+template <class T> DS_HDC T2<T> tri_disk_moment_ol(T ax, T ay, T bx, T by, T r) {
+    T2<T> m;
+    tri_disk_moment(ax, ay, bx, by, r, m.x, m.y);
+    return m;
+}
 template <class T> DS_HDC P3x2<T> lens_grad_ol(P3<T> q2, P3<T> q3, T R1, T R2, T R3) {
     P3x2<T> r;
     lens_grad(q2, q3, R1, R2, R3, r.a, r.b);

@@ -106,3 +106,56 @@ def test_large_cell_takes_the_fused_pass(torch_cuda, orc):
     _, v, gv = gpu_volume(torch_cuda, xyz, r)
     rv, _, rg = orc.Oracle(xyz, r).volumes()
     check(v, gv, rv, rg)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("case", ["globule304", "globule3000", "rna", "large-ball"])
+def test_weighted_volume_gradient(torch_cuda, orc, gen, case, precision):
+    """d(sum_i w_i V_i)/dx for random weights (dsasa_compute_volume_vjp) against the oracle,
+    including the large-capacity pass (a cell too large for the fast pass)."""
+    from paper_2401_10462_gb300 import api
+    torch = torch_cuda
+    if case == "globule304":
+        m = gen.globule(304, 4)
+        xyz, r = m.coords, m.radii
+    elif case == "globule3000":
+        m = gen.globule(3000, 5)
+        xyz, r = m.coords, m.radii
+    elif case == "rna":
+        m = gen.rna(900, 6)
+        xyz, r = m.coords, m.radii
+    else:
+        k = 40
+        idx = np.arange(k) + 0.5
+        z = 1 - 2 * idx / k
+        rr = np.sqrt(1 - z * z)
+        ang = math.pi * (1 + 5 ** 0.5) * idx
+        shell = 5.2 * np.stack([rr * np.cos(ang), rr * np.sin(ang), z], 1)
+        shell = shell[z > -2.0] + 1e-5 * np.random.default_rng(3).normal(size=(int((z > -2.0).sum()), 3))
+        xyz = np.concatenate([np.zeros((1, 3)) + 1e-6, shell])
+        r = np.concatenate([[3.6], np.full(len(shell), 1.2)])
+    n = len(r)
+    w = np.random.default_rng(11).uniform(-1.0, 2.0, n)
+    ctx = api.Context(precision=precision)
+    a = torch.empty(n, dtype=torch.float64, device="cuda")
+    v = torch.empty(n, dtype=torch.float64, device="cuda")
+    gv = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    ctx.compute_volume_vjp(_dev(torch, xyz), _dev(torch, r), _dev(torch, w), a, v, gv)
+    ctx.status_sync()
+    ctx.close()
+    rv, _, rg = orc.Oracle(xyz, r).volumes(weights=w)
+    check(v.cpu().numpy(), gv.cpu().numpy(), rv, rg)
+
+
+def test_volume_autograd(torch_cuda, orc, gen):
+    """molecular_volumes through torch.autograd: the backward of sum_i c_i V_i is the oracle's
+    weighted volume gradient."""
+    from paper_2401_10462_gb300 import autograd as ag
+    torch = torch_cuda
+    m = gen.globule(500, 8)
+    c = np.random.default_rng(2).uniform(0.0, 1.0, m.n)
+    x = torch.as_tensor(m.coords, device="cuda").requires_grad_(True)
+    vol = ag.molecular_volumes(x, torch.as_tensor(m.radii, device="cuda"))
+    (vol * torch.as_tensor(c, device="cuda")).sum().backward()
+    rv, _, rg = orc.Oracle(m.coords, m.radii).volumes(weights=c)
+    check(vol.detach().cpu().numpy(), x.grad.cpu().numpy(), rv, rg)

@@ -113,3 +113,39 @@ def test_volume_rigid_motion(orc, gen):
     q, _ = np.linalg.qr(np.random.default_rng(1).normal(size=(3, 3)))
     v2, tot2, _ = orc.Oracle(m.coords @ q.T + 3.0, m.radii).volumes(grad=False)
     assert np.allclose(v2, v, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("seed", [2, 6])
+def test_weighted_volume_gradient_finite_differences(orc, gen, seed):
+    """d(sum_i w_i V_i)/dx for random weights against central differences of the weighted sum
+    of the per-atom volumes (every component of a sample of atoms), on a small globule."""
+    m = gen.globule(80, seed)
+    w = np.random.default_rng(seed).uniform(-1.0, 2.0, m.n)
+    v0, _, g = orc.Oracle(m.coords, m.radii).volumes(weights=w)
+    h = 1e-5
+    for i in np.random.default_rng(seed + 1).choice(m.n, 12, replace=False):
+        for k in range(3):
+            xp, xm = m.coords.copy(), m.coords.copy()
+            xp[i, k] += h
+            xm[i, k] -= h
+            fd = (w @ orc.Oracle(xp, m.radii).volumes(grad=False)[0] - w @ orc.Oracle(xm, m.radii).volumes(grad=False)[0]) / (2 * h)
+            assert abs(fd - g[i, k]) <= 1e-5 * max(1.0, abs(g[i, k])), (i, k, fd, g[i, k])
+
+
+def test_weighted_volume_gradient_identities(orc, gen):
+    """Unit weights give the union volume's gradient; a weight on one atom alone gives the
+    gradient of that atom's volume, whose entries sum to zero (translation) and whose torque
+    about the origin vanishes (rotation)."""
+    m = gen.globule(150, 9)
+    o = orc.Oracle(m.coords, m.radii)
+    _, _, g1 = o.volumes()
+    _, _, gw = o.volumes(weights=np.ones(m.n))
+    assert np.allclose(gw, g1, rtol=0, atol=1e-11)
+    for i in (3, 77, 140):
+        e = np.zeros(m.n)
+        e[i] = 1.0
+        _, _, gi = o.volumes(weights=e)
+        scale = np.abs(gi).sum()
+        assert scale > 0
+        assert np.abs(gi.sum(0)).max() <= 1e-10 * scale
+        assert np.abs(np.cross(m.coords, gi).sum(0)).max() <= 1e-10 * scale * np.abs(m.coords).max()
