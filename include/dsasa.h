@@ -66,11 +66,15 @@ typedef enum {
  *                 one float-float warp sum; the per-atom constants (multiples of 2 pi R_i^2)
  *                 are added once in FP64.  The gradient is summed in FP32.  Predicates are
  *                 filtered in FP32, then FP64, then decided by exact expansions.
- *                 The gradient contributions of an atom are summed in float-float.  An atom
- *                 whose FP32 contributions cancel too far (a sliver: an exposed area of about
- *                 1e-5 A^2 from terms a million times larger) is detected on the device and
- *                 computed again in FP64 by the large-capacity pass, which in this form runs
- *                 in FP64 for every atom it takes (dsasa_refined_count).
+ *                 The gradient contributions of an atom are summed in float-float (the result
+ *                 does not depend on their order).  The one FP32 quantity that cancels
+ *                 without bound, the height of a triangle's triple points over the plane of
+ *                 its centres (R_i^2 - |z|^2), is taken from the float64 coordinates when its
+ *                 square is below 0.03 R_i^2: the lens gradient is linear in it.
+ *                 Limit: the neighbour vectors enter the terms rounded to float, which leaves
+ *                 an absolute gradient error of about 1e-5 (A^2 / A) per atom; an atom whose
+ *                 gradient is below about 0.02 (nearly buried, or a sliver) can therefore miss
+ *                 a 1e-3 relative bound with a 1e-2 floor.  DSASA_FP64 has no such limit.
  *   DSASA_FP64  - every term in FP64; predicates filtered in FP64, then exact. */
 enum { DSASA_MIXED = 0, DSASA_FP64 = 1 };
 
@@ -165,6 +169,45 @@ dsasa_status dsasa_compute_batch(dsasa_ctx* ctx, int n_mol, const int64_t* atom_
                                  const double* coords, const double* radii, double probe,
                                  const double* area_weights, double* areas_out, double* grad_out);
 
+/* Resident Verlet lists for serving (no paper counterpart; the north star's "neighbour lists
+ * resident on the device across requests"): an arena of capacity_atoms atom slots on
+ * `device` holding, per atom, its candidate list (atoms within R_i + R_j + skin at the
+ * list's build, molecule-local indices), the list length and the coordinates and radius
+ * at the build.  The caller assigns each resident molecule a slot range [base, base + n)
+ * and passes base to dsasa_compute_batch_resident; contexts that share an arena must use
+ * the same skin and probe, and two calls in flight at once must not use the same slots.
+ * A new arena holds no valid list.  dsasa_arena_invalidate marks the lists of a slot range
+ * invalid (asynchronously on `cuda_stream`), as needed when a slot is given to another
+ * molecule.  dsasa_arena_destroy synchronises the device and frees the arena. */
+typedef struct dsasa_arena dsasa_arena;
+dsasa_status dsasa_arena_create(dsasa_arena** out, int device, int64_t capacity_atoms);
+dsasa_status dsasa_arena_invalidate(dsasa_arena* arena, int64_t base, int64_t n, void* cuda_stream);
+void dsasa_arena_destroy(dsasa_arena* arena);
+
+/* The serving form of dsasa_compute_batch (continuous batching; no paper counterpart): one
+ * pass of the kernels over all molecules of the batch, as dsasa_compute_batch, with
+ *   - arena / arena_base: NULL, or the resident lists: arena_base is a HOST array of n_mol
+ *     values, molecule m's first slot in the arena or -1 for a molecule without resident
+ *     lists.  Per molecule the device decides, as for one molecule (see dsasa_config.skin),
+ *     whether its lists can be reused (every atom within skin / 2 of its position at the
+ *     lists' build, radii unchanged, every list valid); reused or rebuilt, the results are the
+ *     same up to rounding.  Needs a context with skin > 0 on the arena's device.
+ *   - mol_ready: NULL, or n_mol int32 (caller memory the device can write: device memory or
+ *     mapped / pinned host memory, zero on entry).  mol_ready[m] becomes 1 once molecule m's
+ *     areas and gradient are final in areas_out / grad_out, while the kernels of the batch are
+ *     still running, so a host polling pinned host memory can return finished molecules early.
+ *     areas_out / grad_out may themselves be mapped host memory (zero-copy outputs).
+ * Every molecule needs at least one atom; the other arguments as dsasa_compute_batch. */
+dsasa_status dsasa_compute_batch_resident(dsasa_ctx* ctx, dsasa_arena* arena, int n_mol,
+                                          const int64_t* atom_offsets, const int64_t* arena_base,
+                                          const double* coords, const double* radii, double probe,
+                                          const double* area_weights, double* areas_out, double* grad_out,
+                                          int32_t* mol_ready);
+
+/* Diagnostics: synchronises and writes, for the n_mol molecules of the last resident batch,
+ * 1 if its lists were reused (0: rebuilt or none). */
+dsasa_status dsasa_batch_reused(dsasa_ctx* ctx, int n_mol, int32_t* reused_host);
+
 /* End-to-end convenience on HOST buffers: copies coords/radii/weights to the device, runs
  * dsasa_compute_vjp, copies areas (and grad if grad_host != NULL) back and synchronises
  * the stream.  Host buffers may be pageable or pinned; weights_host may be NULL. */
@@ -177,18 +220,9 @@ dsasa_status dsasa_compute_host(dsasa_ctx* ctx, const double* coords_host, const
 dsasa_status dsasa_status_sync(dsasa_ctx* ctx);
 
 /* Diagnostics (no paper counterpart): synchronises the stream and writes to *deferred how
- * many atoms of the most recent compute call were finished by the large-capacity pass:
- * atoms whose cell is larger than the fast pass holds (64 neighbour planes or 64 cell
- * vertices) and, in the DSASA_MIXED form, atoms that the cancellation detector handed to
- * that pass (it runs in FP64 there; see dsasa_refined_count). */
+ * many atoms of the most recent compute call had a cell larger than the fast pass holds
+ * (64 neighbour planes or 64 cell vertices) and were finished by the large-capacity pass. */
 dsasa_status dsasa_deferred_count(dsasa_ctx* ctx, int64_t* deferred);
-
-/* Diagnostics (no paper counterpart): synchronises the stream and writes to *refined how
- * many atoms of the most recent DSASA_MIXED compute call had a gradient whose FP32
- * contributions cancel too far for the FP32 form (their summed magnitudes times 2^-20 above a
- * quarter of the gradient tolerance scale 1e-3 max(|g|, 1e-2)): those atoms' outputs were
- * computed again in FP64 by the large-capacity pass. */
-dsasa_status dsasa_refined_count(dsasa_ctx* ctx, int64_t* refined);
 
 /* Per-kernel timing (diagnostics, no paper counterpart).  With timing enabled, each compute
  * call records CUDA events on the context's stream around its kernels; dsasa_kernel_times

@@ -48,10 +48,16 @@ _lib.dsasa_sr_tests.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_lists_reused.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
 _lib.dsasa_compute_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _vp, _vp, ctypes.c_double,
                                      _vp, _vp, _vp]
+_lib.dsasa_arena_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _i64]
+_lib.dsasa_arena_invalidate.argtypes = [_vp, _i64, _i64, _vp]
+_lib.dsasa_arena_destroy.argtypes = [_vp]
+_lib.dsasa_compute_batch_resident.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int64), _vp, _vp, ctypes.c_double, _vp, _vp,
+                                              _vp, _vp]
+_lib.dsasa_batch_reused.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
 _lib.dsasa_compute_host.argtypes = [_vp, _dp, _dp, ctypes.c_double, _i64, _dp, _dp, _dp]
 _lib.dsasa_status_sync.argtypes = [_vp]
 _lib.dsasa_deferred_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
-_lib.dsasa_refined_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_set_timing.argtypes = [_vp, ctypes.c_int]
 _lib.dsasa_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_export_complex.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_int64)]
@@ -64,16 +70,18 @@ _lib.dsasa_destroy.argtypes = [_vp]
 _lib.dsasa_version.restype = ctypes.c_char_p
 for _f in ("dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute", "dsasa_compute_vjp",
            "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync", "dsasa_export_complex",
-           "dsasa_deferred_count", "dsasa_refined_count", "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume",
-           "dsasa_compute_volume_vjp", "dsasa_compute_sr",
+           "dsasa_deferred_count", "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume",
+           "dsasa_compute_volume_vjp", "dsasa_compute_sr", "dsasa_arena_create", "dsasa_arena_invalidate",
+           "dsasa_compute_batch_resident", "dsasa_batch_reused",
            "dsasa_sr_tests", "dsasa_lists_reused"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 EXPORTED = ("dsasa_default_config", "dsasa_create", "dsasa_set_stream", "dsasa_set_precision", "dsasa_compute",
             "dsasa_compute_vjp", "dsasa_compute_batch", "dsasa_compute_host", "dsasa_status_sync",
             "dsasa_export_complex", "dsasa_last_error", "dsasa_destroy", "dsasa_version", "dsasa_deferred_count",
-            "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume", "dsasa_refined_count",
-            "dsasa_compute_volume_vjp",
+            "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume",
+            "dsasa_compute_volume_vjp", "dsasa_arena_create", "dsasa_arena_invalidate", "dsasa_arena_destroy",
+            "dsasa_compute_batch_resident", "dsasa_batch_reused",
             "dsasa_compute_sr", "dsasa_sr_tests", "dsasa_lists_reused", "dsasa_kernel_launches",
             "dsasa_debug_fail_allocations")
 
@@ -237,6 +245,32 @@ class Context:
                                              _ptr(coords), _ptr(radii), float(probe), _ptr(weights), _ptr(areas_out),
                                              _ptr(grad_out)))
 
+    def compute_batch_resident(self, offsets, coords, radii, areas_out, grad_out=None, arena=None,
+                               arena_base=None, mol_ready=None, weights=None, probe: float = PROBE):
+        """dsasa_compute_batch_resident: a batch with optional resident lists (arena: an Arena,
+        arena_base: slot of each molecule or -1) and per-molecule ready flags (mol_ready:
+        int32 tensor of n_mol zeros, device or pinned host).  The output tensors may be
+        pinned host tensors (zero-copy)."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        n_mol = len(off) - 1
+        base = None
+        if arena is not None:
+            base = np.ascontiguousarray(arena_base, dtype=np.int64)
+            if base.shape != (n_mol,):
+                raise ValueError("arena_base needs one entry per molecule")
+        self._sync_stream()
+        p64 = ctypes.POINTER(ctypes.c_int64)
+        self._raise(_lib.dsasa_compute_batch_resident(
+            self._h, arena._h if arena is not None else None, n_mol, off.ctypes.data_as(p64),
+            base.ctypes.data_as(p64) if base is not None else None, _ptr(coords), _ptr(radii), float(probe),
+            _ptr(weights), _ptr(areas_out), _ptr(grad_out), _ptr(mol_ready)))
+
+    def batch_reused(self, n_mol: int) -> np.ndarray:
+        """Per molecule of the last resident batch: whether its lists were reused."""
+        out = np.zeros(max(n_mol, 1), dtype=np.int32)
+        self._raise(_lib.dsasa_batch_reused(self._h, n_mol, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return out[:n_mol].astype(bool)
+
     def compute_host(self, coords, radii, weights=None, grad: bool = True, probe: float = PROBE, out=None):
         """dsasa_compute_host on numpy buffers: copies in, computes, copies out, synchronises."""
         xyz = np.ascontiguousarray(coords, dtype=np.float64)
@@ -276,12 +310,6 @@ class Context:
         self._raise(_lib.dsasa_deferred_count(self._h, ctypes.byref(d)))
         return int(d.value)
 
-    def refined_count(self) -> int:
-        """Atoms of the last mixed-form call recomputed in FP64 (cancellation detector)."""
-        d = ctypes.c_int64(0)
-        self._raise(_lib.dsasa_refined_count(self._h, ctypes.byref(d)))
-        return int(d.value)
-
     def status_code(self) -> int:
         return _lib.dsasa_status_sync(self._h)
 
@@ -301,6 +329,35 @@ class Context:
     def close(self):
         if getattr(self, "_h", None):
             _lib.dsasa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Arena:
+    """A dsasa_arena: resident Verlet lists of molecules kept on one device across calls."""
+
+    def __init__(self, capacity_atoms: int, device: int = 0):
+        h = _vp()
+        st = _lib.dsasa_arena_create(ctypes.byref(h), device, int(capacity_atoms))
+        if st != DSASA_OK:
+            raise DSASAError(st, "dsasa_arena_create failed")
+        self._h = h
+        self.capacity = int(capacity_atoms)
+
+    def invalidate(self, base: int, n: int, stream=None):
+        s = Context._stream_handle(stream)
+        st = _lib.dsasa_arena_invalidate(self._h, int(base), int(n), _vp(s))
+        if st != DSASA_OK:
+            raise DSASAError(st, "dsasa_arena_invalidate failed")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dsasa_arena_destroy(self._h)
             self._h = None
 
     def __del__(self):

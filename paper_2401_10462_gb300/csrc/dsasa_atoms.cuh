@@ -171,12 +171,10 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 template <class R> struct GAcc;
 template <> struct GAcc<float> {
     FF x{0.f, 0.f}, y{0.f, 0.f}, z{0.f, 0.f};
-    float mag = 0.f;   // sum of |contribution| over the components (the cancellation detector)
     __device__ __forceinline__ void add(float a, float b, float c) {
         x = ff_add_f(x, a);
         y = ff_add_f(y, b);
         z = ff_add_f(z, c);
-        mag += fabsf(a) + fabsf(b) + fabsf(c);
     }
     // warp sum (every lane ends with the same value: the float-float sum is commutative)
     __device__ __forceinline__ void reduce(double& gx, double& gy, double& gz) {
@@ -199,15 +197,6 @@ template <> struct GAcc<double> {
         gz = warp_sum_d(z);
     }
 };
-// Cancellation detector of the FP32 form.  An FP32 gradient contribution c carries an error
-// of at most about REFINE_EPS |c| (its geometry, square roots and atan2 in float); the
-// float-float sum adds none of its own.  When REFINE_EPS times the summed magnitudes of an
-// atom's contributions could exceed REFINE_TOL of the gradient tolerance scale
-// max(|g|, 1e-2) (a quarter of the stated 1e-3), the atom is handed to the FP64 pass, whose
-// outputs replace the FP32 ones: such atoms are the slivers whose exposed area and gradient
-// come from terms that cancel many orders of magnitude.
-constexpr float REFINE_EPS = 9.5367431640625e-07f;   // 2^-20 = 16 float ulps of 2^-24
-constexpr double REFINE_TOL = 2.5e-4;
 __device__ __forceinline__ uint8_t tv_get(const uchar4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 template <class SM> __device__ __forceinline__ void ta_set(SM* S, int t, int k, uint8_t s) {
     ((uint8_t*)&S->ta[t & (SM::kNT - 1)])[k] = s;
@@ -489,6 +478,22 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         auto done = [&]() {   // the outputs of this atom are written: tell the terms kernel
             if ((PH == PH_CELL || PH == PH_CLASS || PH == PH_CC) && lane == 0) rec->flag = CELL_DONE;
         };
+        // the outputs of this atom are final (lane 0 wrote them): count it for its molecule
+        // after a system-scope fence; the molecule's last atom raises its ready flag, which a
+        // host may poll in mapped memory while the kernels run
+        auto finished = [&]() {
+            if (A.mol_done && lane == 0) {
+                __threadfence_system();
+                const int m = A.molid[i];
+                const int size = (int)(A.mol_off[m + 1] - A.mol_off[m]);
+                if (atomicAdd(A.mol_done + m, 1) + 1 == size) {
+                    // the molecule's last atom: every other atom of it fenced its outputs before
+                    // counting itself, so the outputs are complete; tell the host
+                    __threadfence_system();
+                    *(volatile int*)(A.mol_ready + m) = 1;
+                }
+            }
+        };
 
         int nc = 0;
         int nrounds = 1;     // vertex-slot rounds in use: slots < 32 * nrounds (warp-uniform)
@@ -530,17 +535,24 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         if constexpr (PH == PH_ALL || PH == PH_CELL || PH == PH_CC) {
         // ---------------- neighbour candidates: balls that may overlap B_i (from this atom's
         // Verlet list when every atom stayed within half the skin of its reference position)
-        const bool reuse = A.reuse != nullptr && *A.reuse != 0;
+        // Verlet lists of one molecule (indexed by atom, scalar reuse flag) or of a batch of
+        // resident molecules (molecule m's lists at its arena slot mol_base[m], entries local
+        // to the molecule, per-molecule reuse flag)
+        const int mi = A.molid[i];
+        const bool slot = A.nbl != nullptr && (A.mol_base == nullptr || A.mol_base[mi] >= 0);
+        const int lofs = A.mol_base ? (int)A.mol_off[mi] : 0;                 // list entry = atom - lofs
+        const size_t li = A.mol_base ? (size_t)(A.mol_base[mi] + (i - lofs)) : (size_t)i;   // list slot of i
+        const bool reuse = slot && (A.mol_base ? A.mol_reuse[mi] != 0 : (A.reuse != nullptr && *A.reuse != 0));
         if (reuse) {
             // the list holds every atom within R_i + R_j + skin at the last rebuild; keep the
             // ones whose balls overlap B_i now (float64, with a relative slack of 1e-9)
-            const int nl = A.nbn[i];
+            const int nl = A.nbn[li];
             for (int b0 = 0; b0 < nl; b0 += 32) {
                 const int k = b0 + lane;
                 bool ok = false;
                 int j = -1;
                 if (k < nl) {
-                    j = A.nbl[(size_t)i * NBL_CAP + k];
+                    j = A.nbl[li * NBL_CAP + k] + lofs;
                     const double dx = A.xyz[3 * j] - c.pi[0], dy = A.xyz[3 * j + 1] - c.pi[1], dz = A.xyz[3 * j + 2] - c.pi[2];
                     const double rr = c.Ri + A.R[j];
                     ok = dx * dx + dy * dy + dz * dz < rr * rr * (1.0 + 1e-9);
@@ -554,7 +566,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             // with Verlet lists (skin > 0) the gather also finds the atoms of the skin band:
             // they go to the atom's list in global memory (nl entries), while the plane table
             // keeps only the balls that overlap B_i now (the float64 test of the reuse path)
-            const bool store_lists = A.nbl != nullptr;
+            const bool store_lists = slot;
             int nl = 0;
             {
                 int cx = min(max((int)floorf((fi.x - G.lo[0]) * G.inv_cell), 0), G.dims[0] - 1);
@@ -577,8 +589,10 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                         if (store_lists) {
                             const unsigned bl = __ballot_sync(FULL, ok);
                             const int lp = nl + __popc(bl & lanemask_lt());
-                            if (ok && lp < NBL_CAP) A.nbl[(size_t)i * NBL_CAP + lp] = j;
+                            if (ok && lp < NBL_CAP) A.nbl[li * NBL_CAP + lp] = j - lofs;
                             nl += __popc(bl);
+                        }
+                        if (store_lists || A.skin_band) {
                             if (ok) {
                                 const double ddx = A.xyz[3 * j] - c.pi[0], ddy = A.xyz[3 * j + 1] - c.pi[1],
                                              ddz = A.xyz[3 * j + 2] - c.pi[2];
@@ -625,11 +639,13 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             if (store_lists && lane == 0) {
                 // the list's length and the reference position for the next calls; a list
                 // longer than its capacity makes the next call rebuild (a deferred atom writes
-                // the same list again in the large-capacity pass)
-                if (nl <= NBL_CAP) A.nbn[i] = nl;
+                // the same list again in the large-capacity pass): one molecule's lists are
+                // all marked by lists_bad, a resident slot's by a negative length
+                if (nl <= NBL_CAP) A.nbn[li] = nl;
+                else if (A.mol_base) A.nbn[li] = -1;
                 else atomicOr(A.lists_bad, 1);
-                for (int k = 0; k < 3; ++k) A.ref_xyz[3 * i + k] = A.xyz[3 * i + k];
-                A.ref_rad[i] = A.radii_in[i];
+                for (int k = 0; k < 3; ++k) A.ref_xyz[3 * li + k] = A.xyz[3 * i + k];
+                A.ref_rad[li] = A.radii_in[i];
             }
         }
         if (nc > KMAX && can_defer) {
@@ -645,6 +661,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
                 if (A.vol) A.vol[i] = __longlong_as_double(0x7ff8000000000000ll);
             }
+            finished();
             done();
             __syncwarp();
             continue;
@@ -954,6 +971,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
                 if (A.vol) A.vol[i] = __longlong_as_double(0x7ff8000000000000ll);
             }
+            finished();
             done();
             __syncwarp();
             continue;
@@ -966,6 +984,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 if (A.vol) A.vol[i] = 0.0;
                 if (A.vgrad) { A.vgrad[3 * i] = A.vgrad[3 * i + 1] = A.vgrad[3 * i + 2] = 0.0; }
             }
+            finished();
             done();
             __syncwarp();
             continue;
@@ -1345,6 +1364,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                     if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
                     if (A.vol) A.vol[i] = __longlong_as_double(0x7ff8000000000000ll);
                 }
+                finished();
                 done();
                 __syncwarp();
                 continue;
@@ -1357,6 +1377,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                     if (A.vol) A.vol[i] = 0.0;
                     if (A.vgrad) { A.vgrad[3 * i] = A.vgrad[3 * i + 1] = A.vgrad[3 * i + 2] = 0.0; }
                 }
+                finished();
                 done();
                 __syncwarp();
                 continue;
@@ -1436,7 +1457,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                     const float2 ra2 = A.Rhl[ga], rb2 = A.Rhl[gb];
                     const FF Ra = {ra2.x, ra2.y}, Rb = {rb2.x, rb2.y};
                     if (part == 3) {
-                        FF v = tri_term_ff_ol(pa, pb, Ri_ff, Ra, Rb, Ri2_ff);
+                        FF v = tri_term_ff_ol(pa, pb, Ri_ff, Ra, Rb, Ri2_ff, -1.f);
                         acc_ff = ff_add(acc_ff, FF{cff * v.h, cff * v.l});
                         cf_sum += cff;
                     }
@@ -1453,13 +1474,29 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 if (GRAD && part < 3) {
                     const P3<R> O = {zero, zero, zero};
                     const R waf = A.w ? (R)A.w[ga] : (R)1, wbf = A.w ? (R)A.w[gb] : (R)1;
+                    // The lens gradient is linear in the height s_t of the triple points over the
+                    // plane of the centres, whose float value (the difference R_i^2 - |z|^2)
+                    // errs by about 2^-24 R_i^2 / s_t: when the float estimate puts s_t^2 below
+                    // 0.03 R_i^2 (about 1 % of the triangles), s_t^2 is taken from the float64
+                    // coordinates (the same for the three owners of the triangle: it depends on
+                    // the three spheres only); an FP64 instruction occupies a GB300 sub-partition
+                    // for 64 cycles, so the FP64 work is kept to those few.
+                    R st = (R)-1;
+                    if constexpr (FFM) {
+                        if (triple_height2(pa, pb, Rr, Raf, Rbf) < (R)0.03 * Rr * Rr) {
+                            const P3<double> qa = {A.xyz[3 * ga] - c.pi[0], A.xyz[3 * ga + 1] - c.pi[1], A.xyz[3 * ga + 2] - c.pi[2]};
+                            const P3<double> qb = {A.xyz[3 * gb] - c.pi[0], A.xyz[3 * gb + 1] - c.pi[1], A.xyz[3 * gb + 2] - c.pi[2]};
+                            const float s2 = (float)triple_height2_ol(qa, qb, c.Ri, A.R[ga], A.R[gb]);
+                            st = s2 > 0.f ? sqrtf(s2) : 0.f;
+                        }
+                    }
                     // owner i: d/dp_i = -(g2 + g3); owner a: p_i is the second centre; owner b
                     const P3<R> u = part == 0 ? pa : (part == 1 ? O - pa : O - pb);
                     const P3<R> w = part == 0 ? pb : (part == 1 ? pb - pa : pa - pb);
                     const R r0 = part == 0 ? Rr : (part == 1 ? Raf : Rbf);
                     const R r1 = part == 0 ? Raf : Rr;
                     const R r2 = part == 2 ? Raf : Rbf;
-                    const P3x2<R> lg = lens_grad_ol(u, w, r0, r1, r2);
+                    const P3x2<R> lg = lens_grad_ol(u, w, r0, r1, r2, st);
                     const R f = cff * (part == 0 ? -wif : (part == 1 ? waf : wbf));
                     R sx = f * (part == 0 ? lg.a.x + lg.b.x : lg.a.x);
                     R sy = f * (part == 0 ? lg.a.y + lg.b.y : lg.a.y);
@@ -1495,19 +1532,6 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             area_acc = warp_sum_d(area_acc);
         }
         if (GRAD) gacc.reduce(gxd, gyd, gzd);
-        if constexpr (FFM && GRAD) {
-            // the FP32 gradient may be too cancellation-prone for this atom: the FP64 pass that
-            // follows (the large-capacity pass) recomputes it; this pass's outputs are replaced
-            if (can_defer) {
-                float mag = gacc.mag;
-                for (int o = 16; o > 0; o >>= 1) mag += __shfl_xor_sync(FULL, mag, o);
-                const double gn = sqrt(gxd * gxd + gyd * gyd + gzd * gzd);
-                if (iK && (double)mag * (double)REFINE_EPS > REFINE_TOL * fmax(gn, 1e-2) && lane == 0) {
-                    A.defer_list[atomicAdd(A.defer_count, 1)] = s;
-                    if (A.refine_count) atomicAdd(A.refine_count, 1);
-                }
-            }
-        }
         __syncwarp();
         if (lane == 0) {
             if (S->bad) {
@@ -1521,6 +1545,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 A.grad[3 * i + 2] = iK ? gzd : 0.0;
             }
         }
+        if (!(PH == PH_ALL && A.vol)) finished();
         if constexpr (PH == PH_ALL) {
             if (A.vol) {
                 if (iK) write_volume(area_acc);
@@ -1641,16 +1666,8 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
         mark(2);
     }
     if (a.defer_list) {
-        if constexpr (sizeof(R) == 4) {
-            // mixed form: the deferred atoms (cells beyond the fast pass's capacity, and atoms
-            // whose FP32 gradient the detector flagged) are computed by the FP64 pass
-            cudaError_t e = launch_large_f64(big, g, big_blocks, s);
-            if (err == cudaSuccess) err = e;
-            note_launches(1);
-        } else {
-            if (g) go(k_atoms<R, true, 128, 128, PH_ALL>, big_blocks, WARPS * 32, big);
-            else go(k_atoms<R, false, 128, 128, PH_ALL>, big_blocks, WARPS * 32, big);
-        }
+        if (g) go(k_atoms<R, true, 128, 128, PH_ALL>, big_blocks, WARPS * 32, big);
+        else go(k_atoms<R, false, 128, 128, PH_ALL>, big_blocks, WARPS * 32, big);
     }
     mark(3);
     return err != cudaSuccess ? err : cudaGetLastError();

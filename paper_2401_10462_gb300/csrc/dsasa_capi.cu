@@ -37,6 +37,18 @@ cudaError_t dev_alloc(void** p, size_t bytes) {
 }
 void dsasa::note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+// Resident Verlet lists of molecules kept on the device across calls (serving): per arena
+// atom, the candidate list (molecule-local indices), its length (negative: no valid list)
+// and the coordinates and radius at the list's build.
+struct dsasa_arena {
+    int device = 0;
+    int64_t cap = 0;
+    int* nbl = nullptr;
+    int* nbn = nullptr;
+    double* ref_xyz = nullptr;
+    double* ref_rad = nullptr;
+};
+
 struct dsasa_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -62,6 +74,11 @@ struct dsasa_ctx {
     unsigned* bsync = nullptr;   // single-molecule build: partial boxes + ticket (zero between calls)
     long long* offsets = nullptr;
     int* defer = nullptr;       // atoms the fast kernel pass defers to the large pass
+    // per-molecule arrays of a batch: arena slot, reuse decision, skin-test scratch, completion
+    long long* mol_base = nullptr;
+    int* mol_reuse = nullptr;
+    int* vmol = nullptr;
+    int* mol_done = nullptr;
     unsigned char* cells = nullptr;   // per-atom cell records between the cell and terms kernels
     // Verlet lists (skin > 0): candidates per atom, reference coordinates / radii, state
     int* nbl = nullptr;
@@ -71,7 +88,7 @@ struct dsasa_ctx {
     int* vstate = nullptr;        // [0] max displacement^2 (float bits), [1] radii changed, [2] reuse, [3] overflow
     int64_t lists_n = 0;          // the lists hold this many atoms of the last single-molecule call
     double lists_probe = -1.0;
-    int* status = nullptr;      // [0] status bits, [1] total cells, [2] deferred count, [3] refined count
+    int* status = nullptr;      // [0] status bits, [1] total cells, [2] deferred count, [3] spare
     // optional per-kernel timing: events of up to kTimingRing calls since the last read
     bool timing = false;
     int n_timed = 0;
@@ -115,7 +132,7 @@ template <class T> void dfree(T*& p) {
 void free_scratch(dsasa_ctx* c) {
     dfree(c->R); dfree(c->Rhl); dfree(c->f4); dfree(c->molid); dfree(c->rank); dfree(c->cell); dfree(c->sidx); dfree(c->sf4);
     dfree(c->bbox); dfree(c->grids); dfree(c->counts); dfree(c->cstart); dfree(c->blocksums); dfree(c->bsync); dfree(c->offsets);
-    dfree(c->defer); dfree(c->cells);
+    dfree(c->defer); dfree(c->cells); dfree(c->mol_base); dfree(c->mol_reuse); dfree(c->vmol); dfree(c->mol_done);
     dfree(c->nbl); dfree(c->nbn); dfree(c->ref_xyz); dfree(c->ref_rad); dfree(c->vstate);
     c->lists_n = 0;
     c->cap_atoms = c->cap_mol = c->cap_cells = 0;
@@ -150,6 +167,7 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
     ALLOC(R, na) ALLOC(Rhl, na) ALLOC(f4, na) ALLOC(molid, na) ALLOC(rank, na) ALLOC(cell, na) ALLOC(sidx, na) ALLOC(sf4, na)
     ALLOC(bbox, 8 * nm) ALLOC(grids, nm) ALLOC(counts, nc + 1) ALLOC(cstart, nc + 1) ALLOC(blocksums, nbs)
     ALLOC(offsets, nm + 1) ALLOC(defer, na) ALLOC(cells, na * (int64_t)cell_record_bytes()) ALLOC(bsync, BUILD_SYNC_WORDS)
+    ALLOC(mol_base, nm) ALLOC(mol_reuse, nm) ALLOC(vmol, 3 * nm) ALLOC(mol_done, nm)
     e = cudaMemsetAsync(c->bsync, 0, sizeof(unsigned) * BUILD_SYNC_WORDS, c->stream);
     if (e != cudaSuccess) { free_scratch(c); return cuda_fail(c, e, "memset"); }
     if (c->cfg.skin > 0.0) {
@@ -184,15 +202,23 @@ cudaError_t build_cells(dsasa_ctx* c, const double* coords, const double* radii,
     return launch_build(b, c->stream);
 }
 
+// the serving extras of a batch: completion flags and resident lists
+struct BatchExtras {
+    int* mol_ready = nullptr;       // caller memory, n_mol ints, zero on entry
+    dsasa_arena* arena = nullptr;   // resident lists (mol_base / mol_reuse already on the device)
+};
+
 dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n, int n_mol,
                  const long long* offsets_dev, const double* w, double* areas, double* grad, int* rec,
-                 int64_t max_rec, double* vol = nullptr, double* vgrad = nullptr, const double* vw = nullptr) {
+                 int64_t max_rec, double* vol = nullptr, double* vgrad = nullptr, const double* vw = nullptr,
+                 const BatchExtras& bx = BatchExtras()) {
     dsasa_status st = ensure(c, n, n_mol);
     if (st != DSASA_OK) return st;
     cudaEvent_t* ev = (c->timing && c->n_timed < kTimingRing) ? c->ev[c->n_timed++] : nullptr;
     if (ev) cudaEventRecord(ev[0], c->stream);
-    // Verlet lists: reused on the device when every atom stayed within half the skin
-    const bool lists = c->nbl != nullptr && n_mol == 1;
+    // Verlet lists of one molecule: reused on the device when every atom stayed within half
+    // the skin (a batch with resident lists decides per molecule before this call)
+    const bool lists = c->nbl != nullptr && n_mol == 1 && bx.arena == nullptr;
     if (lists) {
         const int valid = c->lists_n == n && c->lists_probe == probe;
         cudaError_t ev_e = launch_verlet_check(coords, radii, c->ref_xyz, c->ref_rad, (int)n, valid, c->cfg.skin,
@@ -227,7 +253,6 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     a.nrec = c->nrec;
     a.defer_list = c->defer;
     a.defer_count = c->status + 2;
-    a.refine_count = c->status + 3;
     a.cells = c->cells;
     a.ev = ev ? ev + 2 : nullptr;
     if (lists) {
@@ -238,6 +263,23 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
         a.ref_xyz = c->ref_xyz;
         a.ref_rad = c->ref_rad;
         a.radii_in = radii;
+    }
+    a.skin_band = c->cfg.skin > 0.0;
+    a.mol_off = offsets_dev;
+    if (bx.arena) {
+        a.nbl = bx.arena->nbl;
+        a.nbn = bx.arena->nbn;
+        a.ref_xyz = bx.arena->ref_xyz;
+        a.ref_rad = bx.arena->ref_rad;
+        a.radii_in = radii;
+        a.mol_base = c->mol_base;
+        a.mol_reuse = c->mol_reuse;
+    }
+    if (bx.mol_ready) {
+        e = cudaMemsetAsync(c->mol_done, 0, sizeof(int) * (size_t)n_mol, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+        a.mol_done = c->mol_done;
+        a.mol_ready = bx.mol_ready;
     }
     e = c->cfg.precision == DSASA_FP64 ? launch_atoms_f64(a, grad != nullptr, c->stream)
                                        : launch_atoms_f32(a, grad != nullptr, c->stream);
@@ -426,6 +468,98 @@ dsasa_status dsasa_compute_batch(dsasa_ctx* c, int n_mol, const int64_t* atom_of
     return run(c, coords, radii, probe, n, n_mol, c->offsets, area_weights, areas_out, grad_out, nullptr, 0);
 }
 
+dsasa_status dsasa_arena_create(dsasa_arena** out, int device, int64_t capacity_atoms) {
+    if (!out || capacity_atoms <= 0 || capacity_atoms > 0x3fffffff) return DSASA_ERR_ARG;
+    *out = nullptr;
+    dsasa_arena* r = new (std::nothrow) dsasa_arena();
+    if (!r) return DSASA_ERR_OOM;
+    r->device = device;
+    r->cap = capacity_atoms;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = dev_alloc((void**)&r->nbl, sizeof(int) * (size_t)capacity_atoms * NBL_CAP);
+    if (e == cudaSuccess) e = dev_alloc((void**)&r->nbn, sizeof(int) * (size_t)capacity_atoms);
+    if (e == cudaSuccess) e = dev_alloc((void**)&r->ref_xyz, sizeof(double) * 3 * (size_t)capacity_atoms);
+    if (e == cudaSuccess) e = dev_alloc((void**)&r->ref_rad, sizeof(double) * (size_t)capacity_atoms);
+    if (e == cudaSuccess) e = cudaMemset(r->nbn, 0xff, sizeof(int) * (size_t)capacity_atoms);   // no valid list
+    if (e != cudaSuccess) {
+        dsasa_arena_destroy(r);
+        return e == cudaErrorMemoryAllocation ? DSASA_ERR_OOM : DSASA_ERR_CUDA;
+    }
+    *out = r;
+    return DSASA_OK;
+}
+
+dsasa_status dsasa_arena_invalidate(dsasa_arena* r, int64_t base, int64_t n, void* cuda_stream) {
+    if (!r || base < 0 || n < 0 || base + n > r->cap) return DSASA_ERR_ARG;
+    if (n == 0) return DSASA_OK;
+    cudaError_t e = cudaSetDevice(r->device);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(r->nbn + base, 0xff, sizeof(int) * (size_t)n, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? DSASA_OK : DSASA_ERR_CUDA;
+}
+
+void dsasa_arena_destroy(dsasa_arena* r) {
+    if (!r) return;
+    cudaSetDevice(r->device);
+    cudaDeviceSynchronize();
+    if (r->nbl) cudaFree(r->nbl);
+    if (r->nbn) cudaFree(r->nbn);
+    if (r->ref_xyz) cudaFree(r->ref_xyz);
+    if (r->ref_rad) cudaFree(r->ref_rad);
+    delete r;
+}
+
+dsasa_status dsasa_compute_batch_resident(dsasa_ctx* c, dsasa_arena* arena, int n_mol, const int64_t* atom_offsets,
+                                          const int64_t* arena_base, const double* coords, const double* radii,
+                                          double probe, const double* area_weights, double* areas_out,
+                                          double* grad_out, int32_t* mol_ready) {
+    if (!c) return DSASA_ERR_ARG;
+    if (n_mol < 0 || (n_mol > 0 && !atom_offsets)) return fail(c, DSASA_ERR_ARG, "invalid molecule offsets");
+    if (n_mol == 0) return DSASA_OK;
+    if (atom_offsets[0] != 0) return fail(c, DSASA_ERR_ARG, "atom_offsets[0] must be 0");
+    for (int m = 0; m < n_mol; ++m)
+        if (atom_offsets[m + 1] <= atom_offsets[m]) return fail(c, DSASA_ERR_ARG, "every molecule needs atoms");
+    if ((arena == nullptr) != (arena_base == nullptr)) return fail(c, DSASA_ERR_ARG, "arena and arena_base go together");
+    if (arena) {
+        if (!(c->cfg.skin > 0.0)) return fail(c, DSASA_ERR_ARG, "resident lists need a context with skin > 0");
+        if (arena->device != c->device) return fail(c, DSASA_ERR_ARG, "the arena lives on another device");
+        for (int m = 0; m < n_mol; ++m)
+            if (arena_base[m] >= 0 && arena_base[m] + (atom_offsets[m + 1] - atom_offsets[m]) > arena->cap)
+                return fail(c, DSASA_ERR_CAPACITY, "molecule %d does not fit the arena at %lld", m, (long long)arena_base[m]);
+    }
+    int64_t n = atom_offsets[n_mol];
+    dsasa_status st = check_common(c, coords, radii, probe, n, areas_out);
+    if (st != DSASA_OK) return st;
+    st = ensure(c, n, n_mol);
+    if (st != DSASA_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(c->offsets, atom_offsets, sizeof(long long) * (size_t)(n_mol + 1),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "offsets upload");
+    BatchExtras bx;
+    bx.mol_ready = mol_ready;
+    if (arena) {
+        e = cudaMemcpyAsync(c->mol_base, arena_base, sizeof(long long) * (size_t)n_mol, cudaMemcpyHostToDevice,
+                            c->stream);
+        if (e == cudaSuccess)
+            e = launch_verlet_check_batch(coords, radii, arena->ref_xyz, arena->ref_rad, arena->nbn, c->offsets,
+                                          c->mol_base, (int)n, n_mol, c->cfg.skin, c->vmol, c->mol_reuse, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "resident list check");
+        bx.arena = arena;
+    }
+    return run(c, coords, radii, probe, n, n_mol, c->offsets, area_weights, areas_out, grad_out, nullptr, 0, nullptr,
+               nullptr, nullptr, bx);
+}
+
+dsasa_status dsasa_batch_reused(dsasa_ctx* c, int n_mol, int32_t* reused_host) {
+    if (!c || n_mol < 0 || (n_mol > 0 && !reused_host) || n_mol > c->cap_mol) return DSASA_ERR_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && n_mol > 0)
+        e = cudaMemcpy(reused_host, c->mol_reuse, sizeof(int) * (size_t)n_mol, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reuse flags read");
+    return DSASA_OK;
+}
+
 dsasa_status dsasa_compute_host(dsasa_ctx* c, const double* coords_host, const double* radii_host, double probe,
                                 int64_t n, const double* weights_host, double* areas_host, double* grad_host) {
     dsasa_status st = check_common(c, coords_host, radii_host, probe, n, areas_host);
@@ -488,17 +622,6 @@ dsasa_status dsasa_deferred_count(dsasa_ctx* c, int64_t* deferred) {
     if (e == cudaSuccess) e = cudaMemcpy(h, c->status, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "deferred count read");
     *deferred = h[2];
-    return DSASA_OK;
-}
-
-dsasa_status dsasa_refined_count(dsasa_ctx* c, int64_t* refined) {
-    if (!c || !refined) return DSASA_ERR_ARG;
-    cudaError_t e = cudaSetDevice(c->device);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    int h[4] = {0, 0, 0, 0};
-    if (e == cudaSuccess) e = cudaMemcpy(h, c->status, sizeof(h), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(c, e, "refined count read");
-    *refined = h[3];
     return DSASA_OK;
 }
 

@@ -448,7 +448,55 @@ __global__ void k_verlet_decide(int* vstate, int valid, float lim2) {
     if (!reuse) vstate[3] = 0;   // the lists are rebuilt by this call
 }
 
+// The same test for a batch of resident molecules, per molecule m (atoms [off[m], off[m+1]),
+// lists at arena slot base[m] + local index; base[m] < 0: no lists): vmol[3m] the largest
+// squared displacement since the lists were built (float bits, rounded up), vmol[3m + 1] a
+// radius changed, vmol[3m + 2] some atom has no valid list (negative length).
+__global__ void k_verlet_check_batch(const double* xyz, const double* radii, const double* ref_xyz,
+                                     const double* ref_rad, const int* nbn, const long long* off,
+                                     const long long* base, int n, int n_mol, int* vmol) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = n_mol - 1;   // last m with off[m] <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const int m = lo;
+    if (base[m] < 0) return;
+    const size_t li = (size_t)(base[m] + (i - off[m]));
+    const double dx = xyz[3 * i] - ref_xyz[3 * li], dy = xyz[3 * i + 1] - ref_xyz[3 * li + 1],
+                 dz = xyz[3 * i + 2] - ref_xyz[3 * li + 2];
+    const double dd = dx * dx + dy * dy + dz * dz;
+    const float d2 = dd == dd ? (float)dd * (1.f + 1e-6f) : INFINITY;
+    atomicMax((unsigned*)&vmol[3 * m], __float_as_uint(d2));
+    if (radii[i] != ref_rad[li]) atomicOr(&vmol[3 * m + 1], 1);
+    if (nbn[li] < 0) atomicOr(&vmol[3 * m + 2], 1);
+}
+__global__ void k_verlet_decide_batch(const int* vmol, const long long* base, int n_mol, float lim2, int* reuse) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_mol) return;
+    reuse[m] = base[m] >= 0 && vmol[3 * m + 1] == 0 && vmol[3 * m + 2] == 0 &&
+               __uint_as_float((unsigned)vmol[3 * m]) <= lim2;
+}
+
 }  // namespace
+
+cudaError_t launch_verlet_check_batch(const double* xyz, const double* radii, const double* ref_xyz,
+                                      const double* ref_rad, const int* nbn, const long long* off,
+                                      const long long* base, int n, int n_mol, double skin, int* vmol, int* reuse,
+                                      cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(vmol, 0, sizeof(int) * 3 * (size_t)n_mol, s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        k_verlet_check_batch<<<(n + 255) / 256, 256, 0, s>>>(xyz, radii, ref_xyz, ref_rad, nbn, off, base, n, n_mol, vmol);
+        note_launches(1);
+    }
+    const float lim2 = (float)(0.25 * skin * skin) * (1.f - 1e-6f);
+    k_verlet_decide_batch<<<(n_mol + 127) / 128, 128, 0, s>>>(vmol, base, n_mol, lim2, reuse);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_verlet_check(const double* xyz, const double* radii, const double* ref_xyz, const double* ref_rad,
                                 int n, int valid, double skin, int* vstate, cudaStream_t s) {

@@ -72,7 +72,7 @@ struct BuildArgs {
     double skin;
     const int* skip;   // non-NULL and *skip != 0: the previous cell list is reused (nothing to do)
     int* zero_word;    // non-NULL: zero_word[0..1] set to 0 by the build's first kernel (the next atom
-                       // kernels' deferred count and refined count)
+                       // kernels' deferred count, and a spare word)
     int max_cells;
     // outputs / scratch
     double* R;         // n
@@ -108,6 +108,21 @@ struct AtomArgs {
     double* vol;            // per-atom volumes vol(B_i cap L_i); NULL = not computed
     double* vgrad;          // d(sum_i vw_i V_i) / dx (n x 3); NULL = not computed
     const double* vw;       // volume weights vw (n); NULL = ones (the union volume's gradient)
+    // per-molecule completion (NULL = off; not with volumes): every atom adds 1 to
+    // mol_done[molid] (device memory, zero at the start) once its area and gradient are final,
+    // after a system-scope fence; the molecule's last atom then sets mol_ready[molid] = 1
+    // (caller memory, which may be mapped host memory)
+    int* mol_done;
+    int* mol_ready;
+    const long long* mol_off;   // batch offsets (n_mol + 1, device): molecule m is [off[m], off[m+1])
+    // resident Verlet lists of a batch (NULL = none): molecule m's lists live at arena index
+    // mol_base[m] + (i - mol_off[m]) with molecule-local entries (mol_base[m] < 0: no lists);
+    // mol_reuse[m] != 0: reuse them; an atom whose list overflows marks its slot invalid
+    const long long* mol_base;
+    const int* mol_reuse;
+    // the cell list holds the skin band too (skin > 0): keep only the balls that overlap B_i
+    // now in the plane table
+    int skin_band;
     int n;
     int* status;
     // complex export (NULL = off): records {i, v0, v1, v2, v3}
@@ -118,8 +133,6 @@ struct AtomArgs {
     // large pass reads work_list[0 .. *work_count)
     int* defer_list;
     int* defer_count;       // zero when the first atom kernel starts (cleared by the cell-list build)
-    int* refine_count;      // NULL or the number of atoms the mixed form's detector handed to the
-                            // FP64 pass (zero at the start, cleared with defer_count)
     const int* work_list;
     const int* work_count;
     // per-atom cell records (by sorted position) between the cell kernel and the terms
@@ -167,11 +180,15 @@ cudaError_t launch_build(const BuildArgs& a, cudaStream_t s);
 // reference position, radii unchanged, no list overflow); vstate[0..1] scratch, [3] overflow
 cudaError_t launch_verlet_check(const double* xyz, const double* radii, const double* ref_xyz, const double* ref_rad,
                                 int n, int valid, double skin, int* vstate, cudaStream_t s);
+// the Verlet skin test of a batch of resident molecules: reuse[m] for each molecule (see
+// k_verlet_check_batch); vmol: 3 ints per molecule of scratch
+cudaError_t launch_verlet_check_batch(const double* xyz, const double* radii, const double* ref_xyz,
+                                      const double* ref_rad, const int* nbn, const long long* off,
+                                      const long long* base, int n, int n_mol, double skin, int* vmol, int* reuse,
+                                      cudaStream_t s);
 cudaError_t launch_sr(const SRArgs& a, cudaStream_t s);
 cudaError_t launch_atoms_f32(const AtomArgs& a, bool grad, cudaStream_t s);
 cudaError_t launch_atoms_f64(const AtomArgs& a, bool grad, cudaStream_t s);
-// FP64 large-capacity pass over big.work_list[0 .. *big.work_count) (the mixed form's last kernel)
-cudaError_t launch_large_f64(const AtomArgs& big, bool grad, int blocks, cudaStream_t s);
 size_t scan_scratch_ints(int max_cells);
 size_t cell_record_bytes();
 

@@ -440,8 +440,11 @@ DS_HD double cap64(double d, double R1, double R2) {
 // distance from the centre of sphere 1 to the plane of the circle where spheres 1, 2 meet
 template <class T> DS_HD T t_dist(T d, T R1, T R2) { return (d * d + R1 * R1 - R2 * R2) / ((T)2 * d); }
 
-// one of the two points common to the three sphere surfaces; false if none
-template <class T> DS_HD bool triple_point(P3<T> p1, P3<T> p2, P3<T> p3, T R1, T R2, T R3, P3<T>& x) {
+// one of the two points common to the three sphere surfaces; false if none.  s_ext >= 0
+// replaces the height s of the triple points over the plane of the centres (a value computed
+// more accurately by the caller)
+template <class T> DS_HD bool triple_point(P3<T> p1, P3<T> p2, P3<T> p3, T R1, T R2, T R3, P3<T>& x,
+                                           T s_ext = (T)-1) {
     P3<T> q2 = p2 - p1, q3 = p3 - p1;
     T b2 = (dot3(q2, q2) - R2 * R2 + R1 * R1) * (T)0.5;
     T b3 = (dot3(q3, q3) - R3 * R3 + R1 * R1) * (T)0.5;
@@ -449,9 +452,23 @@ template <class T> DS_HD bool triple_point(P3<T> p1, P3<T> p2, P3<T> p3, T R1, T
     T W = dot3(nn, nn);
     P3<T> z = (cross3(q3, nn) * b2 + cross3(nn, q2) * b3) * ((T)1 / W);
     T psi = dot3(z, z) - R1 * R1;
-    T s = psi < (T)0 ? ds_sqrt(-psi) : (T)0;
+    T s = s_ext >= (T)0 ? s_ext : (psi < (T)0 ? ds_sqrt(-psi) : (T)0);
     x = p1 + z + nn * (s / ds_sqrt(W));
     return psi < (T)0;
+}
+
+// Squared height s^2 = R1^2 - |z|^2 of the triple points of spheres 1, 2, 3 over the plane of
+// their centres (z: the foot of the triple points in that plane, relative to p1; q_k = p_k -
+// p1).  Near a degenerate triangle (the triple points about to merge) this difference cancels:
+// its error is about u R1^2 for inputs rounded to unit roundoff u, so the height, whose error
+// is that over 2 s, is taken from float64 inputs there.
+template <class T> DS_HD T triple_height2(P3<T> q2, P3<T> q3, T R1, T R2, T R3) {
+    const T b2 = (dot3(q2, q2) - R2 * R2 + R1 * R1) * (T)0.5;
+    const T b3 = (dot3(q3, q3) - R3 * R3 + R1 * R1) * (T)0.5;
+    const P3<T> nn = cross3(q2, q3);
+    const T W = dot3(nn, nn);
+    const P3<T> z = (cross3(q3, nn) * b2 + cross3(nn, q2) * b3) * ((T)1 / W);
+    return R1 * R1 - dot3(z, z);
 }
 
 // S_123^(1): area of sphere 1 inside balls 2 and 3 (Eq. trianglev).  With the spherical
@@ -523,7 +540,8 @@ template <class T> DS_HD double tri_term_mixed(P3<T> p2, P3<T> p3, double R1, do
 //   dS/dp2 = (2 R1 / d2) ( -beta_2 t21 n2 + s_t w_2 ),  w_2 = (n3 - g n2) / sqrt(1 - g^2).
 // The half-arc angle is beta_2 = atan2(L, c3 - c2 g), L = (s_t / R1) sqrt(1 - g^2),
 // c_k = t1k / R1, g = n2 . n3.  (Same quantity as differentiating Eq. (trianglev).)
-template <class T> DS_HD void lens_grad(P3<T> q2, P3<T> q3, T R1, T R2, T R3, P3<T>& g2, P3<T>& g3) {
+template <class T> DS_HD void lens_grad(P3<T> q2, P3<T> q3, T R1, T R2, T R3, P3<T>& g2, P3<T>& g3,
+                                        T st_ext = (T)-1) {
     T d2 = norm3(q2), d3 = norm3(q3);
     T t12 = t_dist(d2, R1, R2), t13 = t_dist(d3, R1, R3);
     T c2 = t12 / R1, c3 = t13 / R1;
@@ -533,7 +551,7 @@ template <class T> DS_HD void lens_grad(P3<T> q2, P3<T> q3, T R1, T R2, T R3, P3
     T b2 = (d2 * d2 - R2 * R2 + R1 * R1) * (T)0.5, b3 = (d3 * d3 - R3 * R3 + R1 * R1) * (T)0.5;
     P3<T> z = (cross3(q3, cr) * b2 + cross3(cr, q2) * b3) * ((T)1 / (crn * crn));
     T st2 = R1 * R1 - dot3(z, z);
-    T st = st2 > (T)0 ? ds_sqrt(st2) : (T)0;
+    T st = st_ext >= (T)0 ? st_ext : (st2 > (T)0 ? ds_sqrt(st2) : (T)0);
     T L = (st / R1) * sg;
     T be2 = ds_atan2(L, c3 - c2 * g), be3 = ds_atan2(L, c2 - c3 * g);
     P3<T> n2 = q2 * ((T)1 / d2), n3 = q3 * ((T)1 / d3);
@@ -588,10 +606,10 @@ DS_HD double ff_to_double(FF a) { return (double)a.h + (double)a.l; }
 //   -2 R1 (t12 theta_12 + t13 theta_13) - 2 R1^2 theta_1x
 // with the geometry in float and the radius quantities R1, R1^2 and R1^2 - Rk^2 in
 // float-float; the caller adds c 2 pi R1^2 once per atom in FP64.
-DS_HD FF tri_term_ff(P3<float> p2, P3<float> p3, FF R1, FF R2, FF R3, FF R1sq) {
+DS_HD FF tri_term_ff(P3<float> p2, P3<float> p3, FF R1, FF R2, FF R3, FF R1sq, float s_ext = -1.f) {
     const P3<float> O = {0.f, 0.f, 0.f};
     P3<float> x;
-    triple_point(O, p2, p3, R1.h, R2.h, R3.h, x);
+    triple_point(O, p2, p3, R1.h, R2.h, R3.h, x, s_ext);
     const float e12 = norm3(p2), e13 = norm3(p3);
     const FF w12 = ff_mul(ff_sub(R1, R2), ff_add(R1, R2)), w13 = ff_mul(ff_sub(R1, R3), ff_add(R1, R3));
     const float t12 = ((e12 * e12 + w12.h) + w12.l) * (0.5f / e12);
@@ -711,19 +729,22 @@ template <class T> DS_HDC T solid_angle_half_ol(P3<T> a, P3<T> b, P3<T> c) { ret
 template <class T> DS_HDC double tri_term_mixed_ol(P3<T> p2, P3<T> p3, double R1, double R2, double R3) {
     return tri_term_mixed(p2, p3, R1, R2, R3);
 }
-static DS_HDC FF tri_term_ff_ol(P3<float> p2, P3<float> p3, FF R1, FF R2, FF R3, FF R1sq) {
-    return tri_term_ff(p2, p3, R1, R2, R3, R1sq);
+static DS_HDC FF tri_term_ff_ol(P3<float> p2, P3<float> p3, FF R1, FF R2, FF R3, FF R1sq, float s_ext) {
+    return tri_term_ff(p2, p3, R1, R2, R3, R1sq, s_ext);
 }
 template <class T> DS_HDC T tri_disk_area_ol(T ax, T ay, T bx, T by, T r) { return tri_disk_area(ax, ay, bx, by, r); }
+template <class T> DS_HDC T triple_height2_ol(P3<T> q2, P3<T> q3, T R1, T R2, T R3) {
+    return triple_height2(q2, q3, R1, R2, R3);
+}
 template <class T> struct T2 { T x, y; };
 template <class T> DS_HDC T2<T> tri_disk_moment_ol(T ax, T ay, T bx, T by, T r) {
     T2<T> m;
     tri_disk_moment(ax, ay, bx, by, r, m.x, m.y);
     return m;
 }
-template <class T> DS_HDC P3x2<T> lens_grad_ol(P3<T> q2, P3<T> q3, T R1, T R2, T R3) {
+template <class T> DS_HDC P3x2<T> lens_grad_ol(P3<T> q2, P3<T> q3, T R1, T R2, T R3, T st_ext) {
     P3x2<T> r;
-    lens_grad(q2, q3, R1, R2, R3, r.a, r.b);
+    lens_grad(q2, q3, R1, R2, R3, r.a, r.b, st_ext);
     return r;
 }
 

@@ -92,7 +92,7 @@ extern "C" dsasa_status dsasa_compute_noalloc(const double* coords, const double
     b.cstart = (int*)(base + OFF_CSTART);
     b.blocksums = (int*)(base + OFF_BSUM);
     b.sync = (unsigned*)(base + OFF_SYNC);
-    b.zero_word = status + 2;   // the deferred and refined counts of the atom kernels
+    b.zero_word = status + 2;   // the deferred count of the atom kernels (and a spare word)
     b.status = status;
     b.ncells_out = status + 1;
     if (launch_build(b, s) != cudaSuccess) return DSASA_ERR_CUDA;
@@ -112,7 +112,6 @@ extern "C" dsasa_status dsasa_compute_noalloc(const double* coords, const double
     a.status = status;
     a.defer_list = (int*)(base + OFF_DEFER);
     a.defer_count = status + 2;
-    a.refine_count = status + 3;
     if (launch_atoms_f32(a, grad_out != nullptr, s) != cudaSuccess) return DSASA_ERR_CUDA;
     int h = 0;
     if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return DSASA_ERR_CUDA;

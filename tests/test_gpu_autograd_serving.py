@@ -73,7 +73,14 @@ def test_graphed_trajectory_matches_eager_and_oracle(torch_cuda, orc, gen):
     assert _grad_close(tr.grad.cpu().numpy(), 0.005 * rg)
 
 
-def test_serving_results_same_alone_and_in_the_mix(torch_cuda, gen):
+@pytest.mark.parametrize("resident", [0, 100_000])
+def test_serving_results_same_alone_and_in_the_mix(torch_cuda, gen, resident):
+    """Continuous batching (zero-copy outputs, per-molecule ready flags; with resident
+    Verlet lists or without): every request's outputs equal those of the same request run
+    alone through a fresh server without resident state, bit for bit without resident lists
+    and within the stated tolerances with them (a context with a skin keeps only the balls
+    that overlap in its cells, a plain one also near-tangent ones, which can change the
+    rounding)."""
     torch = torch_cuda
     from paper_2401_10462_gb300 import serve, inputs
     reqs, mols = serve.request_pool(48, seed=3, pool=6, lo=300, hi=6000)
@@ -81,17 +88,68 @@ def test_serving_results_same_alone_and_in_the_mix(torch_cuda, gen):
     t = inputs.poisson_arrivals(len(reqs), rate, seed=1)
     for r_, ti in zip(reqs, t):
         r_.arrival = float(ti)
-    srv = serve.Server(slots=3, slot_atoms=20000)
+    srv = serve.Server(slots=3, slot_atoms=20000, resident_atoms=resident)
     stats = srv.run(reqs)
-    assert stats["requests"] == 48 and stats["p99_ms"] >= stats["p50_ms"] > 0
-    # every request alone through a fresh server gives bit-identical outputs
+    assert stats["requests"] == 48 and stats["failed"] == 0 and stats["p99_ms"] >= stats["p50_ms"] > 0
+    if resident:
+        # frames of a molecule 0.01 A apart: most repeat requests reuse their lists
+        assert stats["lists_reused"] >= 48 - 6 - 10, stats
+    srv.close()
     for q in reqs[:12]:
         alone = serve.Request(q.rid, q.coords, q.radii)
         srv1 = serve.Server(slots=1, slot_atoms=20000)
         srv1.run([alone], realtime=False)
         srv1.close()
-        assert np.array_equal(alone.areas, q.areas) and np.array_equal(alone.grad, q.grad)
-    srv.close()
+        if resident:
+            assert np.all(np.abs(alone.areas - q.areas) <= 1e-4 * np.maximum(alone.areas, 1.0))
+            assert _grad_close(q.grad, alone.grad)
+        else:
+            assert np.array_equal(alone.areas, q.areas) and np.array_equal(alone.grad, q.grad)
+
+
+def test_resident_batch_flags_and_reuse(torch_cuda, gen):
+    """dsasa_compute_batch_resident through the C ABI: zero-copy outputs in pinned host
+    memory match dsasa_compute_batch's within the stated tolerances; every molecule's ready
+    flag is set; the second call
+    with coordinates moved by 0.01 A reuses every molecule's lists, a molecule moved by more
+    than half the skin rebuilds its own, and a molecule without a slot (-1) has none."""
+    torch = torch_cuda
+    from paper_2401_10462_gb300 import api
+    mols = [gen.globule(300, 1), gen.rna(640, 2), gen.globule(1000, 3)]
+    xyz = np.concatenate([m.coords for m in mols])
+    r = np.concatenate([m.radii for m in mols])
+    off = np.cumsum([0] + [m.n for m in mols])
+    n = len(r)
+    ctx = api.Context(skin=1.0)
+    arena = api.Arena(10_000)
+    base = np.array([0, 2000, -1])
+    ha = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hg = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    ready = torch.zeros(3, dtype=torch.int32, pin_memory=True)
+    ref = api.Context()
+    a = torch.empty(n, dtype=torch.float64, device="cuda")
+    g = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(0)
+    for step, shift in enumerate((0.0, 0.01, 0.01)):
+        xyz = xyz + shift * rng.normal(size=xyz.shape)
+        if step == 2:
+            xyz[off[1]:off[2]] += 0.6                     # molecule 1 moves rigidly by more than skin / 2
+        x = torch.as_tensor(xyz, device="cuda")
+        rr = torch.as_tensor(r, device="cuda")
+        ready.zero_()
+        ctx.compute_batch_resident(off, x, rr, ha, hg, arena=arena, arena_base=base, mol_ready=ready)
+        ctx.status_sync()
+        assert ready.tolist() == [1, 1, 1]
+        reused = ctx.batch_reused(3).tolist()
+        assert reused == ([False] * 3 if step == 0 else ([True, True, False] if step == 1 else [True, False, False]))
+        ref.compute_batch(off, x, rr, a, g)
+        ref.status_sync()
+        ra, rg = a.cpu().numpy(), g.cpu().numpy()
+        assert np.all(np.abs(ha.numpy() - ra) <= 1e-4 * np.maximum(ra, 1.0))
+        assert _grad_close(hg.numpy(), rg)
+    ctx.close()
+    ref.close()
+    arena.close()
 
 
 def test_serving_reports_the_failing_request(torch_cuda, gen):
