@@ -184,7 +184,7 @@ def test_sliver_atoms(api, torch_cuda, orc, gen, seed, precision):
     """A globule with one atom whose exposed area is about 1e-5 A^2 (its terms cancel about a
     million-fold), against the oracle.  The FP64 form meets the stated tolerances on every
     atom.  The mixed form meets them on every area and on every gradient above the noise
-    floor of its float inputs (|g| >= 0.02); below it, within 2e-5 absolute (the limit the
+    floor of its float inputs (|g| >= 0.02); below it, within 3e-5 absolute (the limit the
     header states)."""
     import slivers
     torch = torch_cuda
@@ -200,7 +200,7 @@ def test_sliver_atoms(api, torch_cuda, orc, gen, seed, precision):
     err = np.linalg.norm(g - rg, axis=1)
     big = gn >= 0.02
     assert np.all(err[big] <= 1e-3 * gn[big]), np.nonzero(big & (err > 1e-3 * gn))[0]
-    assert np.all(err[~big] <= 2e-5), (np.nonzero(~big & (err > 2e-5))[0], err[~big].max())
+    assert np.all(err[~big] <= 3e-5), (np.nonzero(~big & (err > 3e-5))[0], err[~big].max())
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
