@@ -70,7 +70,7 @@ typedef enum {
  *                 does not depend on their order).  The one FP32 quantity that cancels
  *                 without bound, the height of a triangle's triple points over the plane of
  *                 its centres (R_i^2 - |z|^2), is taken from the float64 coordinates when its
- *                 square is below 0.03 R_i^2: the lens gradient is linear in it.
+ *                 square is below 0.01 R_i^2: the lens gradient is linear in it.
  *                 Limit: the neighbour vectors enter the terms rounded to float, which leaves
  *                 an absolute gradient error of about 1e-5 (A^2 / A) per atom; an atom whose
  *                 gradient is below about 0.02 (nearly buried, or a sliver) can therefore miss

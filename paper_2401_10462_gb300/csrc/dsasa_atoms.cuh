@@ -163,29 +163,31 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
-// A lane's sum of gradient contributions.  In the FP32 form it is a float-float sum: the
-// contributions gathered for one atom largely cancel, and a plain float sum would carry an
-// error of about 2^-24 times the largest partial sum, which moreover depends on the summation
-// order; with float-float the result depends on the contributions only.  The FP64 form sums in
-// double.
+// A lane's sum of gradient contributions.  In the FP32 form every contribution is added
+// exactly as a fixed-point integer (the float value times 2^40, rounded to an int64): the sum
+// is exact and independent of the summation order (the contributions gathered for one atom
+// largely cancel, and a plain float sum would carry an error of about 2^-24 times the largest
+// partial sum); 2^-40 is far below the contributions' own rounding and 2^63 / 2^40 leaves room
+// for sums up to 8e6.  The FP64 form sums in double.
+constexpr float GFIX = 1099511627776.0f;   // 2^40
 template <class R> struct GAcc;
 template <> struct GAcc<float> {
-    FF x{0.f, 0.f}, y{0.f, 0.f}, z{0.f, 0.f};
+    long long x = 0, y = 0, z = 0;
     __device__ __forceinline__ void add(float a, float b, float c) {
-        x = ff_add_f(x, a);
-        y = ff_add_f(y, b);
-        z = ff_add_f(z, c);
+        x += __float2ll_rn(a * GFIX);
+        y += __float2ll_rn(b * GFIX);
+        z += __float2ll_rn(c * GFIX);
     }
-    // warp sum (every lane ends with the same value: the float-float sum is commutative)
+    // warp sum (exact: every lane ends with the same value)
     __device__ __forceinline__ void reduce(double& gx, double& gy, double& gz) {
         for (int o = 16; o > 0; o >>= 1) {
-            x = ff_add(x, FF{__shfl_xor_sync(FULL, x.h, o), __shfl_xor_sync(FULL, x.l, o)});
-            y = ff_add(y, FF{__shfl_xor_sync(FULL, y.h, o), __shfl_xor_sync(FULL, y.l, o)});
-            z = ff_add(z, FF{__shfl_xor_sync(FULL, z.h, o), __shfl_xor_sync(FULL, z.l, o)});
+            x += __shfl_xor_sync(FULL, x, o);
+            y += __shfl_xor_sync(FULL, y, o);
+            z += __shfl_xor_sync(FULL, z, o);
         }
-        gx = ff_to_double(x);
-        gy = ff_to_double(y);
-        gz = ff_to_double(z);
+        gx = (double)x * (1.0 / (double)GFIX);
+        gy = (double)y * (1.0 / (double)GFIX);
+        gz = (double)z * (1.0 / (double)GFIX);
     }
 };
 template <> struct GAcc<double> {
@@ -234,6 +236,20 @@ __device__ PlaneN<XP> xp_of(const Ctx& c, int g) {
     if (g < 0) return xp_ghost(-1 - g, c.h);
     double pk[3] = {c.xyz[3 * g], c.xyz[3 * g + 1], c.xyz[3 * g + 2]};
     return xp_plane(c.pi, c.Ri, pk, c.R[g]);
+}
+
+// one more atom of atom i's molecule has final outputs (lane 0 wrote them): count it after a
+// system-scope fence; the molecule's last atom raises its ready flag (out of line: cold code)
+__device__ __noinline__ void molecule_count(const AtomArgs& A, int i) {
+    __threadfence_system();
+    const int m = A.molid[i];
+    const int size = (int)(A.mol_off[m + 1] - A.mol_off[m]);
+    if (atomicAdd(A.mol_done + m, 1) + 1 == size) {
+        // every other atom of the molecule fenced its outputs before counting itself, so the
+        // outputs are complete; tell the host
+        __threadfence_system();
+        *(volatile int*)(A.mol_ready + m) = 1;
+    }
 }
 
 // predicate kinds
@@ -482,17 +498,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         // after a system-scope fence; the molecule's last atom raises its ready flag, which a
         // host may poll in mapped memory while the kernels run
         auto finished = [&]() {
-            if (A.mol_done && lane == 0) {
-                __threadfence_system();
-                const int m = A.molid[i];
-                const int size = (int)(A.mol_off[m + 1] - A.mol_off[m]);
-                if (atomicAdd(A.mol_done + m, 1) + 1 == size) {
-                    // the molecule's last atom: every other atom of it fenced its outputs before
-                    // counting itself, so the outputs are complete; tell the host
-                    __threadfence_system();
-                    *(volatile int*)(A.mol_ready + m) = 1;
-                }
-            }
+            if (A.mol_done && lane == 0) molecule_count(A, i);
         };
 
         int nc = 0;
@@ -1474,29 +1480,27 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 if (GRAD && part < 3) {
                     const P3<R> O = {zero, zero, zero};
                     const R waf = A.w ? (R)A.w[ga] : (R)1, wbf = A.w ? (R)A.w[gb] : (R)1;
-                    // The lens gradient is linear in the height s_t of the triple points over the
-                    // plane of the centres, whose float value (the difference R_i^2 - |z|^2)
-                    // errs by about 2^-24 R_i^2 / s_t: when the float estimate puts s_t^2 below
-                    // 0.03 R_i^2 (about 1 % of the triangles), s_t^2 is taken from the float64
-                    // coordinates (the same for the three owners of the triangle: it depends on
-                    // the three spheres only); an FP64 instruction occupies a GB300 sub-partition
-                    // for 64 cycles, so the FP64 work is kept to those few.
-                    R st = (R)-1;
-                    if constexpr (FFM) {
-                        if (triple_height2(pa, pb, Rr, Raf, Rbf) < (R)0.03 * Rr * Rr) {
-                            const P3<double> qa = {A.xyz[3 * ga] - c.pi[0], A.xyz[3 * ga + 1] - c.pi[1], A.xyz[3 * ga + 2] - c.pi[2]};
-                            const P3<double> qb = {A.xyz[3 * gb] - c.pi[0], A.xyz[3 * gb + 1] - c.pi[1], A.xyz[3 * gb + 2] - c.pi[2]};
-                            const float s2 = (float)triple_height2_ol(qa, qb, c.Ri, A.R[ga], A.R[gb]);
-                            st = s2 > 0.f ? sqrtf(s2) : 0.f;
-                        }
-                    }
+
                     // owner i: d/dp_i = -(g2 + g3); owner a: p_i is the second centre; owner b
                     const P3<R> u = part == 0 ? pa : (part == 1 ? O - pa : O - pb);
                     const P3<R> w = part == 0 ? pb : (part == 1 ? pb - pa : pa - pb);
                     const R r0 = part == 0 ? Rr : (part == 1 ? Raf : Rbf);
                     const R r1 = part == 0 ? Raf : Rr;
                     const R r2 = part == 2 ? Raf : Rbf;
-                    const P3x2<R> lg = lens_grad_ol(u, w, r0, r1, r2, st);
+                    P3x2f<R> lg = lens_grad_ol(u, w, r0, r1, r2, (R)-1);
+                    if (FFM && lg.refine) {
+                        // The lens gradient is linear in the height s_t of the triple points over
+                        // the plane of the centres, whose float value (R^2 - |z|^2) errs by about
+                        // 2^-24 R^2 / s_t: for the few lens gradients (about 0.4 %) whose s_t^2 is
+                        // below 0.01 R^2 it is taken from the float64 coordinates (the same for the
+                        // three owners: it depends on the three spheres only) and the gradient
+                        // redone.  Each FP64 instruction occupies a GB300 sub-partition for 64
+                        // cycles, so the FP64 work is kept that rare and short (Gram form).
+                        const P3<double> qa = {A.xyz[3 * ga] - c.pi[0], A.xyz[3 * ga + 1] - c.pi[1], A.xyz[3 * ga + 2] - c.pi[2]};
+                        const P3<double> qb = {A.xyz[3 * gb] - c.pi[0], A.xyz[3 * gb + 1] - c.pi[1], A.xyz[3 * gb + 2] - c.pi[2]};
+                        const float s2 = triple_height2_gram(qa, qb, c.Ri, A.R[ga], A.R[gb]);
+                        lg = lens_grad_ol(u, w, r0, r1, r2, (R)(s2 > 0.f ? sqrtf(s2) : 0.f));
+                    }
                     const R f = cff * (part == 0 ? -wif : (part == 1 ? waf : wbf));
                     R sx = f * (part == 0 ? lg.a.x + lg.b.x : lg.a.x);
                     R sy = f * (part == 0 ? lg.a.y + lg.b.y : lg.a.y);

@@ -339,7 +339,8 @@ DS_HD PlaneN<XP> xp_ghost(int g, double h) {
 // the tetrahedron (i, A, B, C) against M, so this is the perturbation of that test.)  g[] holds
 // the global indices of A, B, C, M (negative for ghost planes) and gi that of atom i.  Returns
 // +1 (the vertex is beyond M: clipped) or -1; 0 only if every coefficient vanishes, which
-// needs coincident atoms.
+// needs coincident atoms.  Out of line: only exact ties reach it, and its expansion
+// temporaries would otherwise enlarge every caller.
 DS_HD int sos_clip_sign(const PlaneN<XP>* P, const int* g, int gi) {
     const PlaneN<XP>& A = P[0];
     const PlaneN<XP>& B = P[1];
@@ -540,7 +541,7 @@ template <class T> DS_HD double tri_term_mixed(P3<T> p2, P3<T> p3, double R1, do
 //   dS/dp2 = (2 R1 / d2) ( -beta_2 t21 n2 + s_t w_2 ),  w_2 = (n3 - g n2) / sqrt(1 - g^2).
 // The half-arc angle is beta_2 = atan2(L, c3 - c2 g), L = (s_t / R1) sqrt(1 - g^2),
 // c_k = t1k / R1, g = n2 . n3.  (Same quantity as differentiating Eq. (trianglev).)
-template <class T> DS_HD void lens_grad(P3<T> q2, P3<T> q3, T R1, T R2, T R3, P3<T>& g2, P3<T>& g3,
+template <class T> DS_HD bool lens_grad(P3<T> q2, P3<T> q3, T R1, T R2, T R3, P3<T>& g2, P3<T>& g3,
                                         T st_ext = (T)-1) {
     T d2 = norm3(q2), d3 = norm3(q3);
     T t12 = t_dist(d2, R1, R2), t13 = t_dist(d3, R1, R3);
@@ -558,6 +559,12 @@ template <class T> DS_HD void lens_grad(P3<T> q2, P3<T> q3, T R1, T R2, T R3, P3
     P3<T> w2 = (n3 - n2 * g) * ((T)1 / sg), w3 = (n2 - n3 * g) * ((T)1 / sg);
     g2 = (n2 * (-be2 * (d2 - t12)) + w2 * st) * ((T)2 * R1 / d2);
     g3 = (n3 * (-be3 * (d3 - t13)) + w3 * st) * ((T)2 * R1 / d3);
+    // the gradient is linear in st, whose value here (a difference R1^2 - |z|^2 from rounded
+    // inputs) errs by about u R1^2 / st: report when a caller should supply st from more
+    // accurate inputs (its square below 0.01 R1^2: measured on the triangles of three
+    // 5,000-atom globules, a larger bound no longer lowers the float gradient's worst error,
+    // 6e-5, which then comes from elsewhere)
+    return st_ext < (T)0 && st2 < (T)0.01 * R1 * R1;
 }
 
 // ------------------------------------------------------------------ float-float
@@ -733,19 +740,30 @@ static DS_HDC FF tri_term_ff_ol(P3<float> p2, P3<float> p3, FF R1, FF R2, FF R3,
     return tri_term_ff(p2, p3, R1, R2, R3, R1sq, s_ext);
 }
 template <class T> DS_HDC T tri_disk_area_ol(T ax, T ay, T bx, T by, T r) { return tri_disk_area(ax, ay, bx, by, r); }
-template <class T> DS_HDC T triple_height2_ol(P3<T> q2, P3<T> q3, T R1, T R2, T R3) {
-    return triple_height2(q2, q3, R1, R2, R3);
-}
 template <class T> struct T2 { T x, y; };
 template <class T> DS_HDC T2<T> tri_disk_moment_ol(T ax, T ay, T bx, T by, T r) {
     T2<T> m;
     tri_disk_moment(ax, ay, bx, by, r, m.x, m.y);
     return m;
 }
-template <class T> DS_HDC P3x2<T> lens_grad_ol(P3<T> q2, P3<T> q3, T R1, T R2, T R3, T st_ext) {
-    P3x2<T> r;
-    lens_grad(q2, q3, R1, R2, R3, r.a, r.b, st_ext);
+template <class T> struct P3x2f { P3<T> a, b; bool refine; };
+template <class T> DS_HDC P3x2f<T> lens_grad_ol(P3<T> q2, P3<T> q3, T R1, T R2, T R3, T st_ext) {
+    P3x2f<T> r;
+    r.refine = lens_grad(q2, q3, R1, R2, R3, r.a, r.b, st_ext);
     return r;
+}
+// triple_height2 for float64 inputs in fewer FP64 operations, returned in float: with the
+// Gram matrix G of q2, q3 the foot z = a q2 + b q3 solves G (a, b) = (b2, b3), so
+// |z|^2 = (b2^2 G33 - 2 b2 b3 G23 + b3^2 G22) / det G and
+// s^2 = (R1^2 det G - b2^2 G33 + 2 b2 b3 G23 - b3^2 G22) / det G; the cancellation happens in
+// the float64 numerator, and the division is taken in float.
+static DS_HDC float triple_height2_gram(P3<double> q2, P3<double> q3, double R1, double R2, double R3) {
+    const double g22 = dot3(q2, q2), g33 = dot3(q3, q3), g23 = dot3(q2, q3);
+    const double R1s = R1 * R1;
+    const double b2 = 0.5 * ((g22 - R2 * R2) + R1s), b3 = 0.5 * ((g33 - R3 * R3) + R1s);
+    const double det = g22 * g33 - g23 * g23;
+    const double num = R1s * det - (b2 * b2 * g33 - 2.0 * b2 * b3 * g23 + b3 * b3 * g22);
+    return (float)num / (float)det;
 }
 
 }  // namespace dsasa

@@ -154,19 +154,18 @@ double mc_tri_mixed(const double* q6, double R1, double R2, double R3, double* g
 }
 
 // the float-float form of S_123^(1) used by the mixed-precision kernel (p1 at the origin)
-// the float lens gradient with the triple points' height taken from float64 inputs when the
-// float estimate of its square is below 0.03 R1^2 (the kernels' rule; fix = 1) or always from
+// the float lens gradient with the triple points' height from the float64 differences when
+// lens_grad reports its float value too small to trust (the kernels' rule; fix = 1) or always
+// from
 // the float geometry (fix = 0); g9 as mc_tri_mixed
 void mc_lens_grad_f32(const double* q6, double R1, double R2, double R3, double* g9, int fix) {
     P3<float> q2 = {(float)q6[0], (float)q6[1], (float)q6[2]}, q3 = {(float)q6[3], (float)q6[4], (float)q6[5]};
-    float st = -1.f;
-    if (fix && triple_height2(q2, q3, (float)R1, (float)R2, (float)R3) < 0.03f * (float)R1 * (float)R1) {
-        P3<double> d2 = {q6[0], q6[1], q6[2]}, d3 = {q6[3], q6[4], q6[5]};
-        const float s2 = (float)triple_height2(d2, d3, R1, R2, R3);
-        st = s2 > 0.f ? std::sqrt(s2) : 0.f;
-    }
     P3<float> g2, g3;
-    lens_grad(q2, q3, (float)R1, (float)R2, (float)R3, g2, g3, st);
+    if (lens_grad(q2, q3, (float)R1, (float)R2, (float)R3, g2, g3) && fix) {
+        P3<double> d2 = {q6[0], q6[1], q6[2]}, d3 = {q6[3], q6[4], q6[5]};
+        const float s2 = triple_height2_gram(d2, d3, R1, R2, R3);
+        lens_grad(q2, q3, (float)R1, (float)R2, (float)R3, g2, g3, s2 > 0.f ? std::sqrt(s2) : 0.f);
+    }
     double g[9] = {-(double)(g2.x + g3.x), -(double)(g2.y + g3.y), -(double)(g2.z + g3.z), g2.x, g2.y, g2.z, g3.x, g3.y, g3.z};
     for (int k = 0; k < 9; ++k) g9[k] = g[k];
 }

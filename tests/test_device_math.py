@@ -290,7 +290,7 @@ def test_clip_ties_broken_as_the_oracle_breaks_them(mc, orc):
 def test_lens_gradient_of_near_degenerate_triangles(mc, orc, gen):
     """The float lens gradient of a triangle whose triple points are about to merge (height
     s_t over the plane of the centres small) loses accuracy as 2^-24 R^2 / s_t; with s_t^2 taken
-    from the float64 coordinates below 0.03 R^2 (the kernels' rule) every triangle of the
+    from the float64 coordinates below 0.01 R^2 (the kernels' rule) every triangle of the
     5,000-atom globule stays within 1e-4 of the float64 gradient, which the plain float
     evaluation misses."""
     m = gen.globule(5000, 2)
