@@ -463,15 +463,16 @@ def capsid_measure(args, tm, wm, pk):
 
 def trajectory_measure(args, local):
     """20,000-atom globule, E_np through the autograd Function, Gaussian steps (sigma 0.01 A)
-    replayed from one captured CUDA graph, without and with Verlet-skin lists."""
+    replayed from one captured CUDA graph: cells built afresh every step (no lists), with
+    Verlet-skin lists, and with the lists and carried cells (the incremental update)."""
     import torch
     from paper_2401_10462_gb300 import autograd as ag, inputs
     m = inputs.make("globule", 20000, 0)
     dev = torch.device("cuda", local)
     out = {"workload": "graphed trajectory, 20,000-atom globule, sigma 0.01 A"}
-    for skin in (0.0, 1.0):
+    for name, skin, carry in (("skin_0", 0.0, False), ("skin_1", 1.0, False), ("skin_1_carry", 1.0, True)):
         tr = ag.GraphedTrajectory(torch.as_tensor(m.coords, device=dev), torch.as_tensor(m.radii, device=dev),
-                                  sigma=0.01, seed=0, skin=skin).capture()
+                                  sigma=0.01, seed=0, skin=skin, carry=carry).capture()
         tr.replay(args.warmup)
         torch.cuda.synchronize()
         steps = max(args.steps, 200)
@@ -483,8 +484,18 @@ def trajectory_measure(args, local):
             torch.cuda.synchronize()
         tr.check()
         ms = e0.elapsed_time(e1) / steps
-        out[f"skin_{skin:g}"] = {"steps": steps, "ms_per_step": ms, "atoms_per_s": m.n / ms * 1e3,
-                                 "energy_kcal_mol": tr.energy.item(), "clocks": clk.summary()}
+        out[name] = {"steps": steps, "ms_per_step": ms, "atoms_per_s": m.n / ms * 1e3,
+                     "energy_kcal_mol": tr.energy.item(), "clocks": clk.summary()}
+        if skin > 0:
+            # after the timed region: 100 more steps one at a time, reading the list reuse and
+            # the carried cells of each
+            reused, carried = 0, 0
+            for _ in range(100):
+                tr.replay(1)
+                reused += tr.lib_ctx.lists_reused()
+                carried += tr.lib_ctx.cells_carried()
+            out[name]["steps_reusing_lists"] = reused / 100
+            out[name]["cells_carried_per_step"] = carried / (100 * m.n)
     return out
 
 

@@ -85,14 +85,21 @@ typedef struct {
                          * within R_i + R_j + skin) on the device and reuse them, without
                          * rebuilding the cell list, while every atom stays within skin / 2 of
                          * its position at the last rebuild and n, the radii and the probe are
-                         * unchanged (tested on the device: graph-capturable).  The cells and
-                         * all simplices are recomputed every call; results do not depend on
-                         * reuse beyond rounding. */
+                         * unchanged (tested on the device: graph-capturable).  The simplices
+                         * are recomputed every call; results do not depend on reuse beyond
+                         * rounding. */
     int64_t max_atoms;  /* fixed capacity in atoms, or 0 to grow on demand */
     int64_t max_cells;  /* cap on cell-list cells (0 = default 2^22); larger boxes use coarser cells */
+    int carry;          /* with skin > 0: on calls that reuse the lists, start each atom's cell
+                         * from the one the previous call built (its faces' planes at the current
+                         * positions), kept when exact predicates certify it and then cut by the
+                         * new neighbours; else built afresh.  The incremental update of the
+                         * complex across MD steps of the paper's Conclusions.  Results equal a
+                         * fresh build's up to the rounding of the terms (the simplices of the
+                         * complex are the same).  Default 1. */
 } dsasa_config;
 
-/* Fills cfg with defaults: MIXED, skin 0, grow on demand, default cell cap. */
+/* Fills cfg with defaults: MIXED, skin 0, grow on demand, default cell cap, carry 1. */
 void dsasa_default_config(dsasa_config* cfg);
 
 /* Creates a context on `device` (CUDA ordinal) bound to `cuda_stream` (a cudaStream_t, or
@@ -150,6 +157,10 @@ dsasa_status dsasa_compute_sr(dsasa_ctx* ctx, const double* coords, const double
 /* Diagnostics: synchronises and writes 1 to *reused if the last call reused the Verlet
  * lists (skin > 0), else 0. */
 dsasa_status dsasa_lists_reused(dsasa_ctx* ctx, int* reused);
+
+/* Diagnostics: synchronises and writes the number of atoms whose cell the last call carried
+ * from the previous call (dsasa_config.carry), else 0. */
+dsasa_status dsasa_cells_carried(dsasa_ctx* ctx, int64_t* carried);
 
 /* Diagnostics: synchronises and writes the number of point-neighbour tests the last
  * dsasa_compute_sr call performed (sum over atoms of m x overlapping neighbours). */

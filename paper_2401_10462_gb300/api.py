@@ -31,7 +31,7 @@ PROBE = 1.4
 
 class dsasa_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skin", ctypes.c_double), ("max_atoms", ctypes.c_int64),
-                ("max_cells", ctypes.c_int64)]
+                ("max_cells", ctypes.c_int64), ("carry", ctypes.c_int)]
 
 
 _vp, _dp, _i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
@@ -46,6 +46,7 @@ _lib.dsasa_compute_volume_vjp.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, 
 _lib.dsasa_compute_sr.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, ctypes.c_int, _vp, _vp]
 _lib.dsasa_sr_tests.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_lists_reused.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
+_lib.dsasa_cells_carried.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_compute_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _vp, _vp, ctypes.c_double,
                                      _vp, _vp, _vp]
 _lib.dsasa_arena_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _i64]
@@ -82,7 +83,7 @@ EXPORTED = ("dsasa_default_config", "dsasa_create", "dsasa_set_stream", "dsasa_s
             "dsasa_set_timing", "dsasa_kernel_times", "dsasa_compute_volume",
             "dsasa_compute_volume_vjp", "dsasa_arena_create", "dsasa_arena_invalidate", "dsasa_arena_destroy",
             "dsasa_compute_batch_resident", "dsasa_batch_reused",
-            "dsasa_compute_sr", "dsasa_sr_tests", "dsasa_lists_reused", "dsasa_kernel_launches",
+            "dsasa_compute_sr", "dsasa_sr_tests", "dsasa_lists_reused", "dsasa_cells_carried", "dsasa_kernel_launches",
             "dsasa_debug_fail_allocations")
 
 
@@ -122,13 +123,14 @@ class Context:
     """One dsasa_ctx bound to a device and a stream (default: torch's current stream)."""
 
     def __init__(self, device: int = 0, stream=None, precision: str | int = "mixed", skin: float = 0.0,
-                 max_atoms: int = 0, max_cells: int = 0):
+                 max_atoms: int = 0, max_cells: int = 0, carry: bool = True):
         cfg = dsasa_config()
         _lib.dsasa_default_config(ctypes.byref(cfg))
         cfg.precision = precision if isinstance(precision, int) else {"mixed": DSASA_MIXED, "fp64": DSASA_FP64}[precision]
         cfg.skin = float(skin)
         cfg.max_atoms = int(max_atoms)
         cfg.max_cells = int(max_cells)
+        cfg.carry = int(bool(carry))
         self.device = device
         h = _vp()
         st = _lib.dsasa_create(ctypes.byref(h), device, _vp(self._stream_handle(stream)), ctypes.byref(cfg))
@@ -226,6 +228,12 @@ class Context:
         r = ctypes.c_int(0)
         self._raise(_lib.dsasa_lists_reused(self._h, ctypes.byref(r)))
         return bool(r.value)
+
+    def cells_carried(self) -> int:
+        """Atoms whose cell the last call carried from the previous call (skin > 0, carry on)."""
+        t = ctypes.c_int64(0)
+        self._raise(_lib.dsasa_cells_carried(self._h, ctypes.byref(t)))
+        return int(t.value)
 
     def sr_tests(self) -> int:
         """Point-neighbour tests of the last compute_sr call."""

@@ -24,8 +24,10 @@
 // through a per-atom record in HBM (PH_CELL: Step 1; PH_CLASS: Step 2; PH_TERMS: Step 3;
 // PH_VOL: the volume), so that each kernel's code fits the instruction cache.  When all atoms
 // fit in one wave, Steps 1 and 2 run as one kernel (PH_CC), so that classifications overlap
-// the slowest cells.  The fused form (PH_ALL) serves the large-capacity pass and the
-// no-allocation entry point.
+// the slowest cells.  With carried cells, Step 1 is PH_CARRY (on calls reusing the neighbour
+// lists, each atom's cell from the previous call, kept when exact predicates certify it) and
+// then PH_CELL over the atoms it could not keep.  The fused form (PH_ALL) serves the
+// large-capacity pass and the no-allocation entry point.
 #pragma once
 #include "dsasa_kernels.cuh"
 #include "dsasa_math.cuh"
@@ -50,7 +52,7 @@ constexpr int MINB = 32, MINB_CELL = 18, MINB_CLASS = 18, MINB_TERMS = 18;
 // through a global record per atom: the cell construction (gather, sort, clipping), the
 // classification (Steps 2a-2c: which simplices of the cell are in C), and the area terms and
 // gradient.  Each kernel's code then fits the instruction cache.
-enum { PH_ALL = 0, PH_CELL = 1, PH_CLASS = 2, PH_TERMS = 3, PH_VOL = 4, PH_CC = 5 };
+enum { PH_ALL = 0, PH_CELL = 1, PH_CLASS = 2, PH_TERMS = 3, PH_VOL = 4, PH_CC = 5, PH_CARRY = 6 };
 enum { CELL_OK = 0, CELL_DONE = 1 };   // record flag: CELL_DONE = outputs already written
 
 // Per-warp cell storage.  NE plane entries (0..5 ghosts, then the candidates in sorted
@@ -96,7 +98,8 @@ template <class R, int NE, int NT> struct CellRec {
     uint8_t tf[NT];
     uint8_t eflag[NE];
     int iK, icl;
-    int nc, hw, flag, pad;
+    int nc, hw, flag;
+    int atom;             // the atom whose cell this is (-1: no cell), for carrying it to the next call
 };
 using CellRecF = CellRec<float, 64, 64>;
 using CellRecD = CellRec<double, 64, 64>;
@@ -448,15 +451,198 @@ template <class SM, class R = typename SM::Real> __device__ __forceinline__ P3<R
     return {S->pq[e][0], S->pq[e][1], S->pq[e][2]};
 }
 
+// ------------------------------------------------------------------ carried cells
+// The incremental update of C across MD steps.  On a call that reuses the neighbour lists
+// (every atom within half the skin of its last rebuild), the cell that the previous call
+// built for atom i is carried to the current positions when exact predicates certify it,
+// instead of being clipped again from the cube.
+//
+// Any set F of planes of other atoms may bound the cell: each half-space contains the true
+// Laguerre cell, and the half-space of an atom whose ball does not meet B_i contains B_i, so
+// the cell cut by F and by the current candidates meets B_i exactly where the cell of the
+// candidates does (its vertices inside B_i, and so every simplex of C, are the same).  The
+// record gives F (the previous cell's faces, ghosts included) and the dual triangulation of
+// their polytope.  With every vertex recomputed from its three current planes, the structure
+// is that polytope when (i) every vertex has a certified positive orientation and (ii) every
+// vertex lies strictly inside every other face plane of F.  Then each vertex is a simple
+// vertex of the polytope, and its edge along the line of two of its planes ends at the
+// structure's neighbour across that edge: both lie on the line, each strictly inside the
+// other's third plane and strictly inside every remaining plane.  The structure, closed under
+// that adjacency, holds every vertex of the polytope (whose vertex-edge graph is connected),
+// and the polytope is bounded.  When, in addition, no current candidate outside F removes a
+// vertex, the structure is the cell.  The carry kernel (PH_CARRY) keeps exactly those cells;
+// every other atom (no usable record, a failed certification, a new candidate that cuts, or
+// lists not reused) goes to a redo list that the plain cell kernel then builds from the cube,
+// so the carry kernel holds no clipping code.
+//
+// carry_cell reads the record, checks its structure (plane ids in range, every edge's two
+// triangles pointing at each other with the edge reversed, every face's start slot on that
+// face, V = 2F - 4 for the closed triangulation of a sphere), renumbers the faces NG.. in
+// record order with the other candidates after them, and sets up the shared tables:
+// triangles, adjacency, free slots (the dead slots below the high-water mark), the test order
+// (ghost faces, faces, other candidates) and each face's start slot, staged in rem[] for the
+// caller.  It returns nc | ncert << 8 | nclip << 16 | nalive << 24, or 0 when the record
+// gives no usable structure.
+template <class SM, class RC>
+__device__ __noinline__ int carry_cell(SM* S, const RC* rec, int i, int n, int nc, int lane) {
+    constexpr int NE = SM::kNE, NT = SM::kNT, KMAX = NE - NG;
+    static_assert(NE == 64 && NT == 64, "the record is read as two entries per lane; start slots are staged in rem");
+    // every load of the record at once, one memory round trip (the arrays are read whole;
+    // entries past the record's counts are ignored)
+    const int4 hd = *reinterpret_cast<const int4*>(&rec->iK);   // iK, icl, nc, hw
+    const int tag = rec->atom;
+    int rpg[2];
+    uint8_t rst[2];
+    uchar4 rtv[2], rta[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int e = lane + 32 * h;
+        rpg[h] = rec->pg[e];
+        rst[h] = rec->start[e];
+        rtv[h] = rec->tv[e];
+        rta[h] = rec->ta[e];
+    }
+    const int nco = hd.z, hwo = hd.w;
+    if (tag != i || nco < 0 || nco > KMAX || hwo < 4 || hwo > NT) return 0;
+    const int npo = NG + nco;
+    const uchar4 none = make_uchar4(NONE, NONE, NONE, 0);
+    for (int k = lane; k < nc; k += 32) S->bedge[k] = (unsigned)S->pg[NG + k];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int e = lane + 32 * h;
+        if (e < npo) {
+            S->skey[e] = (unsigned)rpg[h];
+            S->bslot[e] = rst[h];
+            S->eslot[e] = NONE;
+        }
+        S->tv[e] = e < hwo ? rtv[h] : none;
+        S->ta[e] = e < hwo ? rta[h] : none;
+        S->rem[e] = NONE;
+        S->kf[e] = 0;
+        S->tf[e] = 0;
+    }
+    __syncwarp();
+    bool ok = true;
+    int live = 0;
+    for (int t = lane; t < hwo; t += 32) {
+        const uchar4 v = S->tv[t];
+        if (v.x == NONE) continue;
+        ++live;
+        if (v.x >= npo || v.y >= npo || v.z >= npo || v.x == v.y || v.y == v.z || v.z == v.x) {
+            ok = false;
+            continue;
+        }
+        S->eslot[v.x] = 1;
+        S->eslot[v.y] = 1;
+        S->eslot[v.z] = 1;
+        const uchar4 adj = S->ta[t];
+        for (int k = 0; k < 3; ++k) {
+            const int t2 = tv_get(adj, k);
+            if (t2 >= hwo) { ok = false; break; }
+            const uchar4 w = S->tv[t2];
+            const uint8_t a = tv_get(v, k), b = tv_get(v, (k + 1) % 3);
+            int k2 = -1;
+            for (int h = 0; h < 3; ++h)
+                if (tv_get(w, h) == b && tv_get(w, (h + 1) % 3) == a) k2 = h;
+            if (k2 < 0 || tv_get(S->ta[t2], k2) != t) { ok = false; break; }
+        }
+    }
+    ok = __all_sync(FULL, ok);
+    live = warp_sum_i(live);
+    __syncwarp();
+    if (!ok) return 0;
+    // the faces: ghosts keep their ids, the others become NG, NG + 1, ... (record order);
+    // each face's start slot must be a live triangle of that face
+    int nF = 0, ngf = 0;
+    for (int e0 = 0; e0 < npo; e0 += 32) {
+        const int e = e0 + lane;
+        const bool f = e < npo && S->eslot[e] == 1;
+        if (f) {
+            const int st = S->bslot[e];
+            const uchar4 v = st < hwo ? S->tv[st] : none;
+            if (!(v.x == e || v.y == e || v.z == e)) ok = false;
+        }
+        const unsigned bg = __ballot_sync(FULL, f && e < NG), ba = __ballot_sync(FULL, f && e >= NG);
+        if (f && e >= NG) {
+            const int r = nF + __popc(ba & lanemask_lt());
+            const int g = (int)S->skey[e];
+            if (g < 0 || g >= n || g == i) ok = false;
+            S->pg[NG + r] = g;
+            S->rem[NG + r] = S->bslot[e];
+            S->eslot[e] = (uint8_t)(NG + r);
+        } else if (f) {
+            S->rem[e] = S->bslot[e];
+            S->eslot[e] = (uint8_t)e;
+        } else if (e < npo) {
+            S->eslot[e] = NONE;
+        }
+        nF += __popc(ba);
+        ngf += __popc(bg);
+    }
+    ok = __all_sync(FULL, ok) && live == 2 * (nF + ngf) - 4;
+    if (!ok) return 0;
+    __syncwarp();
+    // the current candidates that are not faces, after the faces
+    int nnew = 0;
+    for (int k0 = 0; k0 < nc; k0 += 32) {
+        const int k = k0 + lane;
+        int g = -1;
+        bool add = false;
+        if (k < nc) {
+            g = (int)S->bedge[k];
+            add = true;
+            for (int f = 0; f < nF; ++f)
+                if (S->pg[NG + f] == g) add = false;
+        }
+        const unsigned bn = __ballot_sync(FULL, add);
+        const int r = nF + nnew + __popc(bn & lanemask_lt());
+        if (add && r < KMAX) S->pg[NG + r] = g;
+        nnew += __popc(bn);
+    }
+    const int ncn = nF + nnew;
+    if (ncn > KMAX) return 0;
+    // clipping order: ghost faces, faces, new candidates
+    {
+        const bool gf = lane < NG && S->eslot[lane] != NONE;
+        const unsigned bg = __ballot_sync(FULL, gf);
+        if (gf) S->ord[__popc(bg & lanemask_lt())] = (uint8_t)lane;
+    }
+    for (int k = lane; k < ncn; k += 32) S->ord[ngf + k] = (uint8_t)(NG + k);
+    // triangles in the new numbering; the dead slots below the high-water mark are free
+    int nfree = 0;
+    for (int t0 = 0; t0 < hwo; t0 += 32) {
+        const int t = t0 + lane;
+        bool dead = false;
+        if (t < hwo) {
+            const uchar4 v = S->tv[t];
+            if (v.x == NONE) dead = true;
+            else S->tv[t] = make_uchar4(S->eslot[v.x], S->eslot[v.y], S->eslot[v.z], 0);
+        }
+        const unsigned bd = __ballot_sync(FULL, dead);
+        if (dead) S->fs[nfree + __popc(bd & lanemask_lt())] = (uint8_t)t;
+        nfree += __popc(bd);
+    }
+    if (lane == 0) {
+        S->hw = hwo;
+        S->nfree = nfree;
+        S->bad = 0;
+    }
+    __syncwarp();
+    return ncn | (ngf + nF) << 8 | (ngf + ncn) << 16 | live << 24;
+}
+
 // ------------------------------------------------------------------ the kernel
 __host__ __device__ constexpr int minb(int ph) {
-    return (ph == PH_CELL || ph == PH_CC) ? MINB_CELL : (ph == PH_CLASS ? MINB_CLASS : ((ph == PH_TERMS || ph == PH_VOL) ? MINB_TERMS : MINB));
+    return (ph == PH_CELL || ph == PH_CC || ph == PH_CARRY) ? MINB_CELL : (ph == PH_CLASS ? MINB_CLASS : ((ph == PH_TERMS || ph == PH_VOL) ? MINB_TERMS : MINB));
 }
 __host__ __device__ constexpr int warps_of(int ph) {
-    return (ph == PH_CELL || ph == PH_CC) ? WARPS_CELL : (ph == PH_CLASS ? WARPS_CLASS : ((ph == PH_TERMS || ph == PH_VOL) ? WARPS_TERMS : WARPS));
+    return (ph == PH_CELL || ph == PH_CC || ph == PH_CARRY) ? WARPS_CELL : (ph == PH_CLASS ? WARPS_CLASS : ((ph == PH_TERMS || ph == PH_VOL) ? WARPS_TERMS : WARPS));
 }
-template <class R, bool GRAD, int NE, int NT, int PH>
-__global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs A) {
+template <class R, bool GRAD, int NE, int NT, int PHX>
+__global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArgs A) {
+    // PH_CARRY: the carried cells of list-reusing calls (the other atoms go to the redo list)
+    constexpr bool CARRY = PHX == PH_CARRY;
+    constexpr int PH = CARRY ? PH_CELL : PHX;
     constexpr int WARPS = warps_of(PH);
     constexpr int SPL = NT / 32;      // vertex slots per lane
     constexpr int KMAX = NE - NG;     // overlapping neighbours per atom
@@ -493,6 +679,14 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         CellRec<R, NE, NT>* rec = (CellRec<R, NE, NT>*)A.cells + s;
         auto done = [&]() {   // the outputs of this atom are written: tell the terms kernel
             if ((PH == PH_CELL || PH == PH_CLASS || PH == PH_CC) && lane == 0) rec->flag = CELL_DONE;
+        };
+        auto no_cell = [&]() {   // the record holds no cell of this atom (nothing to carry)
+            if ((PH == PH_CELL || PH == PH_CC) && lane == 0) rec->atom = -1;
+        };
+        // PH_CARRY: this atom's cell is built by the cell kernel that follows, from the redo list
+        auto redo = [&]() {
+            if (lane == 0) A.redo_list[atomicAdd(A.redo_count, 1)] = s;
+            __syncwarp();
         };
         // the outputs of this atom are final (lane 0 wrote them): count it for its molecule
         // after a system-scope fence; the molecule's last atom raises its ready flag, which a
@@ -549,6 +743,9 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         const int lofs = A.mol_base ? (int)A.mol_off[mi] : 0;                 // list entry = atom - lofs
         const size_t li = A.mol_base ? (size_t)(A.mol_base[mi] + (i - lofs)) : (size_t)i;   // list slot of i
         const bool reuse = slot && (A.mol_base ? A.mol_reuse[mi] != 0 : (A.reuse != nullptr && *A.reuse != 0));
+        if constexpr (CARRY) {
+            if (!reuse) { redo(); continue; }
+        }
         if (reuse) {
             // the list holds every atom within R_i + R_j + skin at the last rebuild; keep the
             // ones whose balls overlap B_i now (float64, with a relative slack of 1e-9)
@@ -654,8 +851,12 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 A.ref_rad[li] = A.radii_in[i];
             }
         }
+        if constexpr (CARRY) {
+            if (nc > KMAX) { redo(); continue; }
+        }
         if (nc > KMAX && can_defer) {
             if (lane == 0) A.defer_list[atomicAdd(A.defer_count, 1)] = s;
+            no_cell();
             done();
             __syncwarp();
             continue;
@@ -667,10 +868,24 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
                 if (A.vol) A.vol[i] = __longlong_as_double(0x7ff8000000000000ll);
             }
+            no_cell();
             finished();
             done();
             __syncwarp();
             continue;
+        }
+
+        // ---------------- PH_CARRY: the previous call's cell carried over (list-reusing calls);
+        // an atom whose record gives no usable structure, or whose carried cell is not certified
+        // or is cut by a new candidate, goes to the redo list
+        constexpr bool carried = CARRY;
+        int ncert = 0, nclip = nc;   // planes that certify the carried cell; the other candidates
+        if constexpr (CARRY) {
+            const int cc = carry_cell(S, rec, i, A.n, nc, lane);
+            if (cc == 0) { redo(); continue; }
+            nc = cc & 255;
+            ncert = (cc >> 8) & 255;
+            nclip = (cc >> 16) & 255;
         }
 
         // ---------------- plane table: ghosts 0..5, candidates NG..NG+nc-1; sort keys
@@ -700,6 +915,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             S->eflag[e] = 0;
         }
         __syncwarp();
+        if constexpr (!carried) {
         for (int r = 0; r < SPL; ++r) {
             int el = r * 32 + lane;
             if (el < nc) {
@@ -811,17 +1027,67 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
         }
         if (lane < NG) S->start[lane] = (lane & 1) ? 7 : 0;   // +x,+y,+z at corner 0; -x,-y,-z at 7
         __syncwarp();
+        } else {
+            // the carried faces' start slots (staged by carry_cell), the clipping marks cleared
+            for (int e = lane; e < NG + nc; e += 32) S->start[e] = S->rem[e];
+            __syncwarp();
+            for (int t = lane; t < NT; t += 32) S->rem[t] = 0;
+            __syncwarp();
+        }
 
+        const int hw0 = carried ? S->hw : 8;
+        nrounds = (hw0 + 31) >> 5;
 #pragma unroll
         for (int r = 0; r < SPL; ++r) {
             int t = r * 32 + lane;
-            if (t < 8) { compute_vertex(r, t); alive |= 1u << r; }
+            if (t < hw0 && (!CARRY || S->tv[t].x != NONE)) { compute_vertex(r, t); alive |= 1u << r; }
+        }
+        bool empty = false;
+        int nalive = 8;      // live cell vertices (warp-uniform)
+        if constexpr (CARRY) {
+            // the certification: (i) every carried vertex has a certified positive orientation;
+            // (ii) every face plane keeps every vertex not on it strictly inside.  The new
+            // candidates are tested in the same sweep (planes outer, the lane's vertices inner,
+            // one warp vote at the end): one that removes a vertex sends the atom to the redo list,
+            // and so does any test that the FP32 (FP64) filter leaves open
+            bool fail = false, cut = false;
+#pragma unroll
+            for (int r = 0; r < SPL; ++r) {
+                if (!(alive >> r & 1)) continue;
+                FA<R> D;
+                D.v = V[r][3];
+                if constexpr (LOOSE) D.a = Vs[r];
+                else D.a = Va[r][3];
+                if (fa_sign(D, Gam<R>::g, Gam<R>::tiny) <= 0) fail = true;
+            }
+            for (int kk = 0; kk < nclip; ++kk) {
+                const int m = S->ord[kk] & (NE - 1);
+                const bool cert = kk < ncert;
+                const PlaneN<FA<R>> M = fplane(S, m);
+                const R qmax = fmax(fmax(M.q.x.a, M.q.y.a), fmax(M.q.z.a, M.b.a));
+#pragma unroll
+                for (int r = 0; r < SPL; ++r) {
+                    if (r >= nrounds) break;
+                    if (!(alive >> r & 1)) continue;
+                    const uchar4 v = S->tv[r * 32 + lane];
+                    if (cert && (v.x == m || v.y == m || v.z == m)) continue;   // a vertex on the face
+                    FA<R> sv;
+                    sv.v = M.q.x.v * V[r][0] + M.q.y.v * V[r][1] + M.q.z.v * V[r][2] - M.b.v * V[r][3];
+                    if constexpr (LOOSE) sv.a = qmax * Vs[r];
+                    else sv.a = M.q.x.a * Va[r][0] + M.q.y.a * Va[r][1] + M.q.z.a * Va[r][2] + M.b.a * Va[r][3];
+                    // the filters only: a test they leave open sends the atom to the redo
+                    // list (no call in the loop; such tests are rare)
+                    const int sg = fa_sign(sv, Gam<R>::gclip, Gam<R>::tiny);
+                    if (sg > 0 && !cert) cut = true;
+                    else if (sg >= 0) fail = true;
+                }
+            }
+            if (__any_sync(FULL, fail || cut)) { redo(); continue; }
         }
 
         // ---------------- clipping by the sorted neighbour planes
-        bool empty = false;
-        int nalive = 8;      // live cell vertices (warp-uniform)
-        for (int kk = 0; kk < nc && !empty; ++kk) {
+        if constexpr (!CARRY) {
+        for (int kk = 0; kk < nclip && !empty; ++kk) {
             const int m = S->ord[kk] & (NE - 1);
             const PlaneN<FA<R>> M = fplane(S, m);
             // sum_k |q_k| a_k <= max_k |q_k| * sum_k a_k: the loose magnitude of the clip test
@@ -962,10 +1228,12 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
             }
             __syncwarp();
         }
+        }
         __syncwarp();
         const bool bad = S->bad != 0;
         if (bad && S->bad == 2 && can_defer) {
             if (lane == 0) A.defer_list[atomicAdd(A.defer_count, 1)] = s;
+            no_cell();
             done();
             __syncwarp();
             continue;
@@ -977,6 +1245,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 if (A.grad) { A.grad[3 * i] = A.grad[3 * i + 1] = A.grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll); }
                 if (A.vol) A.vol[i] = __longlong_as_double(0x7ff8000000000000ll);
             }
+            no_cell();
             finished();
             done();
             __syncwarp();
@@ -990,6 +1259,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 if (A.vol) A.vol[i] = 0.0;
                 if (A.vgrad) { A.vgrad[3 * i] = A.vgrad[3 * i + 1] = A.vgrad[3 * i + 2] = 0.0; }
             }
+            no_cell();
             finished();
             done();
             __syncwarp();
@@ -1012,6 +1282,7 @@ __global__ void __launch_bounds__(warps_of(PH) * 32, minb(PH)) k_atoms(AtomArgs 
                 rec->nc = nc;
                 rec->hw = hw;
                 rec->flag = CELL_OK;
+                rec->atom = i;
             }
             __syncwarp();
             if constexpr (PH == PH_CELL) continue;
@@ -1648,12 +1919,22 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     };
     if (a.cells) {
         auto nb = [&](int w) { return (a.n + w - 1) / w; };
-        if (cells_in_one_wave<R>(a.n)) {
+        if (cells_in_one_wave<R>(a.n) && !a.carry) {
             go(k_atoms<R, false, 64, 64, PH_CC>, nb(WARPS_CELL), WARPS_CELL * 32, fast);
             mark(0);
             mark(1);
         } else {
-            go(k_atoms<R, false, 64, 64, PH_CELL>, nb(WARPS_CELL), WARPS_CELL * 32, fast);
+            if (a.carry) {
+                // the carried cells, then the cell kernel over the redo list (its grid covers
+                // every atom; the warps past the list's length return at once)
+                go(k_atoms<R, false, 64, 64, PH_CARRY>, nb(WARPS_CELL), WARPS_CELL * 32, fast);
+                AtomArgs redo = fast;
+                redo.work_list = a.redo_list;
+                redo.work_count = a.redo_count;
+                go(k_atoms<R, false, 64, 64, PH_CELL>, nb(WARPS_CELL), WARPS_CELL * 32, redo);
+            } else {
+                go(k_atoms<R, false, 64, 64, PH_CELL>, nb(WARPS_CELL), WARPS_CELL * 32, fast);
+            }
             mark(0);
             go(k_atoms<R, false, 64, 64, PH_CLASS>, nb(WARPS_CLASS), WARPS_CLASS * 32, fast);
             mark(1);

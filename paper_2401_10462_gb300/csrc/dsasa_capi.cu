@@ -74,6 +74,8 @@ struct dsasa_ctx {
     unsigned* bsync = nullptr;   // single-molecule build: partial boxes + ticket (zero between calls)
     long long* offsets = nullptr;
     int* defer = nullptr;       // atoms the fast kernel pass defers to the large pass
+    int* redo = nullptr;        // atoms whose cell the carry kernel could not keep
+    int64_t carry_n = 0;        // atoms of the last call when it carried cells, else 0
     // per-molecule arrays of a batch: arena slot, reuse decision, skin-test scratch, completion
     long long* mol_base = nullptr;
     int* mol_reuse = nullptr;
@@ -88,7 +90,7 @@ struct dsasa_ctx {
     int* vstate = nullptr;        // [0] max displacement^2 (float bits), [1] radii changed, [2] reuse, [3] overflow
     int64_t lists_n = 0;          // the lists hold this many atoms of the last single-molecule call
     double lists_probe = -1.0;
-    int* status = nullptr;      // [0] status bits, [1] total cells, [2] deferred count, [3] spare
+    int* status = nullptr;      // [0] status bits, [1] total cells, [2] deferred count, [3] redo count
     // optional per-kernel timing: events of up to kTimingRing calls since the last read
     bool timing = false;
     int n_timed = 0;
@@ -132,7 +134,7 @@ template <class T> void dfree(T*& p) {
 void free_scratch(dsasa_ctx* c) {
     dfree(c->R); dfree(c->Rhl); dfree(c->f4); dfree(c->molid); dfree(c->rank); dfree(c->cell); dfree(c->sidx); dfree(c->sf4);
     dfree(c->bbox); dfree(c->grids); dfree(c->counts); dfree(c->cstart); dfree(c->blocksums); dfree(c->bsync); dfree(c->offsets);
-    dfree(c->defer); dfree(c->cells); dfree(c->mol_base); dfree(c->mol_reuse); dfree(c->vmol); dfree(c->mol_done);
+    dfree(c->defer); dfree(c->redo); dfree(c->cells); dfree(c->mol_base); dfree(c->mol_reuse); dfree(c->vmol); dfree(c->mol_done);
     dfree(c->nbl); dfree(c->nbn); dfree(c->ref_xyz); dfree(c->ref_rad); dfree(c->vstate);
     c->lists_n = 0;
     c->cap_atoms = c->cap_mol = c->cap_cells = 0;
@@ -166,7 +168,7 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
     if (e != cudaSuccess) { free_scratch(c); return cuda_fail(c, e, "cudaMalloc " #ptr); }
     ALLOC(R, na) ALLOC(Rhl, na) ALLOC(f4, na) ALLOC(molid, na) ALLOC(rank, na) ALLOC(cell, na) ALLOC(sidx, na) ALLOC(sf4, na)
     ALLOC(bbox, 8 * nm) ALLOC(grids, nm) ALLOC(counts, nc + 1) ALLOC(cstart, nc + 1) ALLOC(blocksums, nbs)
-    ALLOC(offsets, nm + 1) ALLOC(defer, na) ALLOC(cells, na * (int64_t)cell_record_bytes()) ALLOC(bsync, BUILD_SYNC_WORDS)
+    ALLOC(offsets, nm + 1) ALLOC(defer, na) ALLOC(redo, na) ALLOC(cells, na * (int64_t)cell_record_bytes()) ALLOC(bsync, BUILD_SYNC_WORDS)
     ALLOC(mol_base, nm) ALLOC(mol_reuse, nm) ALLOC(vmol, 3 * nm) ALLOC(mol_done, nm)
     e = cudaMemsetAsync(c->bsync, 0, sizeof(unsigned) * BUILD_SYNC_WORDS, c->stream);
     if (e != cudaSuccess) { free_scratch(c); return cuda_fail(c, e, "memset"); }
@@ -265,6 +267,9 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
         a.radii_in = radii;
     }
     a.skin_band = c->cfg.skin > 0.0;
+    a.carry = lists && c->cfg.carry != 0;
+    a.redo_list = c->redo;
+    a.redo_count = c->status + 3;   // cleared by the cell-list build
     a.mol_off = offsets_dev;
     if (bx.arena) {
         a.nbl = bx.arena->nbl;
@@ -286,6 +291,7 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
     if (e != cudaSuccess) return cuda_fail(c, e, "atom kernel launch");
     // the lists now describe this call's molecule (or none: another layout overwrote the cells)
     c->lists_n = lists ? n : 0;
+    c->carry_n = a.carry ? n : 0;
     c->lists_probe = probe;
     return DSASA_OK;
 }
@@ -311,6 +317,7 @@ void dsasa_default_config(dsasa_config* cfg) {
     cfg->skin = 0.0;
     cfg->max_atoms = 0;
     cfg->max_cells = 0;
+    cfg->carry = 1;
 }
 
 const char* dsasa_version(void) { return kVersion; }
@@ -434,6 +441,18 @@ dsasa_status dsasa_lists_reused(dsasa_ctx* c, int* reused) {
     if (e == cudaSuccess) e = cudaMemcpy(h, c->vstate, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "list state read");
     *reused = h[2];
+    return DSASA_OK;
+}
+
+dsasa_status dsasa_cells_carried(dsasa_ctx* c, int64_t* carried) {
+    if (!c || !carried) return DSASA_ERR_ARG;
+    *carried = 0;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    int h = 0;
+    if (e == cudaSuccess && c->carry_n > 0) e = cudaMemcpy(&h, c->status + 3, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "redo count read");
+    *carried = c->carry_n > 0 ? c->carry_n - h : 0;   // every atom is carried or redone
     return DSASA_OK;
 }
 

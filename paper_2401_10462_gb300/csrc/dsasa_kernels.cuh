@@ -123,6 +123,13 @@ struct AtomArgs {
     // the cell list holds the skin band too (skin > 0): keep only the balls that overlap B_i
     // now in the plane table
     int skin_band;
+    // single-molecule calls with neighbour lists: the carry kernel keeps each atom's cell from
+    // the previous call where it can (list-reusing calls) and appends the other atoms (sorted
+    // positions) to redo_list, counted in *redo_count (zero when the kernels start); the cell
+    // kernel then builds those
+    int carry;
+    int* redo_list;
+    int* redo_count;
     int n;
     int* status;
     // complex export (NULL = off): records {i, v0, v1, v2, v3}

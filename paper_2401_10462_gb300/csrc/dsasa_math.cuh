@@ -339,8 +339,7 @@ DS_HD PlaneN<XP> xp_ghost(int g, double h) {
 // the tetrahedron (i, A, B, C) against M, so this is the perturbation of that test.)  g[] holds
 // the global indices of A, B, C, M (negative for ghost planes) and gi that of atom i.  Returns
 // +1 (the vertex is beyond M: clipped) or -1; 0 only if every coefficient vanishes, which
-// needs coincident atoms.  Out of line: only exact ties reach it, and its expansion
-// temporaries would otherwise enlarge every caller.
+// needs coincident atoms.
 DS_HD int sos_clip_sign(const PlaneN<XP>* P, const int* g, int gi) {
     const PlaneN<XP>& A = P[0];
     const PlaneN<XP>& B = P[1];

@@ -1,0 +1,169 @@
+"""Carried cells, the incremental update of the complex across MD steps: on calls that reuse
+the neighbour lists, each atom's cell starts from the one the previous call built (its faces'
+planes at the current positions), is kept when exact predicates certify it, and is then cut by
+the new neighbours; a cell that fails the certification is built from the cube.  The
+simplices of C must be exactly the oracle's at every step, the areas and gradient those of a
+fresh build up to the rounding of the terms, and most cells must carry over small steps."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2401_10462_gb300 import api
+    return api
+
+
+def _sets(rec):
+    out = {d: set() for d in range(4)}
+    owners = {}
+    for r in rec:
+        simp = tuple(int(x) for x in r[1:] if x >= 0)
+        out[len(simp) - 1].add(simp)
+        owners.setdefault(simp, set()).add(int(r[0]))
+    return out, owners
+
+
+def _check_against_oracle(orc, rec, x, r):
+    got, owners = _sets(rec)
+    o = orc.Oracle(x, r)
+    for d in range(4):
+        ref = {tuple(int(v) for v in np.atleast_1d(s)) for s in o.simplices(d)}
+        assert got[d] == ref, (d, len(got[d]), len(ref), list(got[d] ^ ref)[:5])
+    for simp, who in owners.items():
+        assert who == set(simp), (simp, who)
+
+
+def _run(torch, ctx, x, r, weights=None):
+    n = len(r)
+    a = torch.empty(n, dtype=torch.float64, device="cuda")
+    g = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    ctx.compute(torch.as_tensor(x, device="cuda"), torch.as_tensor(r, device="cuda"), a, g)
+    carried = ctx.cells_carried()
+    reused = ctx.lists_reused()
+    ctx.status_sync()
+    return a.cpu().numpy(), g.cpu().numpy(), carried, reused
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_carried_complex_is_the_oracles(api, torch_cuda, orc, gen, precision):
+    """Three steps of 0.02 A rms per coordinate on a 3,000-atom globule: the complex that the
+    carried cells give is exactly the oracle's at each step (about 45 % of the cells carry over
+    steps this large)."""
+    torch = torch_cuda
+    m = gen.globule(3000, 4)
+    rng = np.random.default_rng(7)
+    ctx = api.Context(precision=precision, skin=1.0)
+    r = torch.as_tensor(m.radii, device="cuda")
+    x = m.coords.copy()
+    ctx.export_complex(torch.as_tensor(x, device="cuda"), r)   # builds the lists and the cells
+    assert ctx.cells_carried() == 0
+    for _ in range(3):
+        x = x + rng.normal(scale=0.02, size=x.shape)
+        rec = ctx.export_complex(torch.as_tensor(x, device="cuda"), r).cpu().numpy()
+        carried = ctx.cells_carried()
+        assert ctx.lists_reused()
+        ctx.status_sync()
+        _check_against_oracle(orc, rec, x, m.radii)
+        assert carried >= 0.3 * m.n, carried
+    ctx.close()
+
+
+def test_carry_matches_fresh_cells(api, torch_cuda, orc, gen):
+    """Ten steps of 0.01 A on a 2,000-atom globule: carried cells, lists without carrying and
+    a context without lists agree up to the rounding of the terms; the last step also against
+    the oracle."""
+    torch = torch_cuda
+    m = gen.globule(2000, 9)
+    rng = np.random.default_rng(5)
+    carry = api.Context(skin=1.0)
+    plain = api.Context(skin=1.0, carry=False)
+    fresh = api.Context()
+    x = m.coords.copy()
+    for step in range(11):
+        if step:
+            x = x + rng.normal(scale=0.01, size=x.shape)
+        a, g, nc, reused = _run(torch, carry, x, m.radii)
+        ap, gp, ncp, _ = _run(torch, plain, x, m.radii)
+        af, gf, _, _ = _run(torch, fresh, x, m.radii)
+        assert reused == (step > 0)
+        assert ncp == 0
+        assert (nc == 0) if step == 0 else (nc >= 0.6 * m.n), (step, nc)
+        for aa, gg in ((a, g), (ap, gp)):
+            assert np.all(np.abs(aa - af) <= 1e-5 * np.maximum(af, 1.0))
+            assert abs(aa.sum() - af.sum()) <= 1e-8 * af.sum()
+            err = np.linalg.norm(gg - gf, axis=1)
+            assert np.all(err <= 1e-3 * np.maximum(np.linalg.norm(gf, axis=1), 1e-2))
+    ra, _, rg = orc.sasa(x, m.radii)
+    assert np.all(np.abs(a - ra) <= 1e-4 * np.maximum(ra, 1.0))
+    assert abs(a.sum() - ra.sum()) <= 1e-6 * ra.sum()
+    err = np.linalg.norm(g - rg, axis=1)
+    assert np.all(err <= 1e-3 * np.maximum(np.linalg.norm(rg, axis=1), 1e-2))
+    for c in (carry, plain, fresh):
+        c.close()
+
+
+def test_same_positions_carry_every_cell(api, torch_cuda, orc, gen):
+    """Unchanged coordinates: every cell of the previous call certifies (all vertices lie
+    strictly inside their other face planes, or on them with the same tie-break), so every
+    atom with a cell carries it; areas equal the first call's up to summation order."""
+    torch = torch_cuda
+    m = gen.globule(1500, 3)
+    ctx = api.Context(skin=0.8)
+    a0, g0, nc0, _ = _run(torch, ctx, m.coords, m.radii)
+    a1, g1, nc1, reused = _run(torch, ctx, m.coords, m.radii)
+    assert nc0 == 0 and reused
+    assert nc1 >= np.count_nonzero(a0 > 0), (nc1, np.count_nonzero(a0 > 0))
+    assert np.all(np.abs(a1 - a0) <= 1e-9 * np.maximum(a0, 1.0))
+    assert np.all(np.linalg.norm(g1 - g0, axis=1) <= 1e-6 * np.maximum(np.linalg.norm(g0, axis=1), 1e-2))
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["lattice", "cospherical"])
+def test_degenerate_inputs_carry_consistently(api, torch_cuda, orc, case):
+    """Exactly degenerate inputs (every vertex on more than three bisectors) called twice:
+    the certification meets exact ties, which the same Simulation of Simplicity decides, and
+    the complex stays the oracle's."""
+    torch = torch_cuda
+    if case == "lattice":
+        g = np.stack(np.meshgrid(np.arange(4), np.arange(4), np.arange(3), indexing="ij"), -1).reshape(-1, 3)
+        x, r = g * 2.5, np.full(len(g), 1.5)
+    else:
+        c = np.array([[a, b, d] for a in (-1.5, 1.5) for b in (-1.5, 1.5) for d in (-1.5, 1.5)])
+        f = np.array([[3.5, 0, 0], [-3.5, 0, 0], [0, 3.5, 0], [0, -3.5, 0], [0, 0, 3.5], [0, 0, -3.5]])
+        x = np.concatenate([[[0.0, 0.0, 0.0]], c, f]) + np.array([4.0, -2.0, 1.5])
+        r = np.concatenate([[1.2], np.full(8, 1.5), np.full(6, 1.7)])
+    ctx = api.Context(skin=0.5)
+    xt, rt = torch.as_tensor(x, device="cuda"), torch.as_tensor(r, device="cuda")
+    for call in range(2):
+        rec = ctx.export_complex(xt, rt).cpu().numpy()
+        assert ctx.lists_reused() == (call == 1)
+        ctx.status_sync()
+        _check_against_oracle(orc, rec, x, r)
+    ctx.close()
+
+
+def test_rebuild_carries_nothing(api, torch_cuda, gen):
+    """A step that rebuilds the lists (one atom moved by more than half the skin) builds every
+    cell afresh; so does a context with carrying off."""
+    torch = torch_cuda
+    m = gen.globule(1000, 2)
+    ctx = api.Context(skin=1.0)
+    x = m.coords.copy()
+    _run(torch, ctx, x, m.radii)
+    x[10] += np.array([0.0, 0.7, 0.0])
+    _, _, nc, reused = _run(torch, ctx, x, m.radii)
+    assert not reused and nc == 0
+    _, _, nc, reused = _run(torch, ctx, x, m.radii)
+    assert reused and nc > 0
+    ctx.close()

@@ -1,7 +1,9 @@
 """The differentiation workload: a 20,000-atom globule, E_np = sum 0.005 A_i through the
 autograd Function, 1,000 Gaussian steps (sigma = 0.01 A per coordinate) replayed from one
 captured CUDA graph; at steps 0, 100, ..., 1000 the gradient of 64 seeded atoms is checked
-against central finite differences (h = 1e-4 A) of the FP64 oracle's total area.
+against central finite differences (h = 1e-4 A) of the FP64 oracle's total area.  Run twice:
+cells built afresh every step, and with a 1 A Verlet skin, where steps that reuse the lists
+carry each atom's cell from the previous step (the incremental update of the complex).
 
 The oracle runs on local patches: the outputs that depend on p_j are the areas of the
 atoms whose balls overlap B_j, and those depend only on the balls overlapping them, so the
@@ -51,7 +53,8 @@ def pool():
     p.join()
 
 
-def test_graphed_trajectory_fd(pool, orc, gen):
+@pytest.mark.parametrize("skin", [0.0, 1.0])
+def test_graphed_trajectory_fd(pool, orc, gen, skin):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -65,7 +68,7 @@ def test_graphed_trajectory_fd(pool, orc, gen):
     e, _ = ag.nonpolar_energy(xr, r)
     e.backward()
     checkpoints = [(0, x0.cpu().numpy(), xr.grad.cpu().numpy())]
-    tr = ag.GraphedTrajectory(x0, r, sigma=0.01, seed=11).capture()
+    tr = ag.GraphedTrajectory(x0, r, sigma=0.01, seed=11, skin=skin).capture()
     for step in range(100, 1001, 100):
         tr.replay(100)
         torch.cuda.synchronize()
