@@ -1085,35 +1085,41 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
             if (__any_sync(FULL, fail || cut)) { redo(); continue; }
         }
 
-        // ---------------- clipping by the sorted neighbour planes
+        // ---------------- clipping by the sorted neighbour planes.  The loop makes no call on
+        // the clip tests: a test that the filter leaves open ends the inner loop, that plane's
+        // tests are resolved outside it (tight magnitudes, then exact predicates), and the loop
+        // resumes at the same plane with the resolved signs.  (A call inside the loop made the
+        // compiler keep the loop's state in local memory.)
         if constexpr (!CARRY) {
-        for (int kk = 0; kk < nclip && !empty; ++kk) {
+        int kk = 0;
+        unsigned rsv = 0;          // removal bits of plane kk resolved outside the loop
+        bool resolved = false, open_tests = false;
+        for (;;) {
+        for (; kk < nclip && !empty; ++kk) {
             const int m = S->ord[kk] & (NE - 1);
-            const PlaneN<FA<R>> M = fplane(S, m);
-            // sum_k |q_k| a_k <= max_k |q_k| * sum_k a_k: the loose magnitude of the clip test
-            const R qmax = fmax(fmax(M.q.x.a, M.q.y.a), fmax(M.q.z.a, M.b.a));
             unsigned remv = 0;
+            if (resolved) {
+                remv = rsv;
+                resolved = false;
+            } else {
+                const PlaneN<FA<R>> M = fplane(S, m);
+                // sum_k |q_k| a_k <= max_k |q_k| * sum_k a_k: the loose magnitude of the clip test
+                const R qmax = fmax(fmax(M.q.x.a, M.q.y.a), fmax(M.q.z.a, M.b.a));
+                bool open = false;
 #pragma unroll
-            for (int r = 0; r < SPL; ++r) {
-                if (r >= nrounds) break;
-                if (!(alive >> r & 1)) continue;
-                FA<R> sv;
-                sv.v = M.q.x.v * V[r][0] + M.q.y.v * V[r][1] + M.q.z.v * V[r][2] - M.b.v * V[r][3];
-                if constexpr (LOOSE) sv.a = qmax * Vs[r];
-                else sv.a = M.q.x.a * Va[r][0] + M.q.y.a * Va[r][1] + M.q.z.a * Va[r][2] + M.b.a * Va[r][3];
-                int sg = fa_sign(sv, Gam<R>::gclip, Gam<R>::tiny);
-                if (LOOSE && sg == 0) {
-                    const uchar4 v = S->tv[r * 32 + lane];
-                    const VtxFA<R> q = vertex_fa(S, v);
-                    sv.a = M.q.x.a * q.a[0] + M.q.y.a * q.a[1] + M.q.z.a * q.a[2] + M.b.a * q.a[3];
-                    sg = fa_sign(sv, Gam<R>::gclip, Gam<R>::tiny);
+                for (int r = 0; r < SPL; ++r) {
+                    if (r >= nrounds) break;
+                    if (!(alive >> r & 1)) continue;
+                    FA<R> sv;
+                    sv.v = M.q.x.v * V[r][0] + M.q.y.v * V[r][1] + M.q.z.v * V[r][2] - M.b.v * V[r][3];
+                    if constexpr (LOOSE) sv.a = qmax * Vs[r];
+                    else sv.a = M.q.x.a * Va[r][0] + M.q.y.a * Va[r][1] + M.q.z.a * Va[r][2] + M.b.a * Va[r][3];
+                    const int sg = fa_sign(sv, Gam<R>::gclip, Gam<R>::tiny);
+                    if (sg > 0) remv |= 1u << r;
+                    else if (sg == 0) open = true;
                 }
-                if (sg == 0) {
-                    const uchar4 v = S->tv[r * 32 + lane];
-                    sg = resolve_exact(c, PK_CLIP, S->pg[v.x & (NE - 1)], S->pg[v.y & (NE - 1)],
-                                       S->pg[v.z & (NE - 1)], S->pg[m], Gam<R>::try64);
-                }
-                if (sg > 0) remv |= 1u << r;
+                open_tests = __any_sync(FULL, open);
+                if (open_tests) break;
             }
             unsigned bal[SPL];
             int nrem = 0;
@@ -1227,6 +1233,29 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                 }
             }
             __syncwarp();
+        }
+        if (!open_tests) break;
+        // the tests of plane kk that the filter left open: tight magnitudes, then exact
+        {
+            open_tests = false;
+            const int m = S->ord[kk] & (NE - 1);
+            const PlaneN<FA<R>> M = fplane(S, m);
+            rsv = 0;
+            for (int r = 0; r < nrounds; ++r) {
+                if (!(alive >> r & 1)) continue;
+                const uchar4 v = S->tv[r * 32 + lane];
+                const VtxFA<R> q = vertex_fa(S, v);
+                FA<R> sv;
+                sv.v = M.q.x.v * q.v[0] + M.q.y.v * q.v[1] + M.q.z.v * q.v[2] - M.b.v * q.v[3];
+                sv.a = M.q.x.a * q.a[0] + M.q.y.a * q.a[1] + M.q.z.a * q.a[2] + M.b.a * q.a[3];
+                int sg = fa_sign(sv, Gam<R>::gclip, Gam<R>::tiny);
+                if (sg == 0)
+                    sg = resolve_exact(c, PK_CLIP, S->pg[v.x & (NE - 1)], S->pg[v.y & (NE - 1)],
+                                       S->pg[v.z & (NE - 1)], S->pg[m], Gam<R>::try64);
+                if (sg > 0) rsv |= 1u << r;
+            }
+            resolved = true;
+        }
         }
         }
         __syncwarp();
