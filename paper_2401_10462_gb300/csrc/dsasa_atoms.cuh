@@ -446,6 +446,13 @@ __device__ __noinline__ int psign(const SM* S, const Ctx& c, const FA<R>& wi, in
     return resolve_exact(c, kind, S->pg[e0 & M], S->pg[e1 & M], S->pg[e2 & M], S->pg[e3 & M], Gam<R>::try64);
 }
 
+// the filter alone (inline): the certified sign, or 0 when the filter leaves it open
+template <int KIND, class SM, class R = typename SM::Real>
+__device__ __forceinline__ int fsign(const SM* S, const FA<R>& wi, int e0, int e1, int e2 = 0) {
+    PlaneN<FA<R>> P[4] = {fplane(S, e0), fplane(S, e1), fplane(S, e2), fplane(S, e2)};
+    return fa_sign(eval_k<KIND>(P, wi), Gam<R>::g, Gam<R>::tiny);
+}
+
 template <class SM, class R = typename SM::Real> __device__ __forceinline__ P3<R> ppos(const SM* S, int e) {
     e &= SM::kNE - 1;
     return {S->pq[e][0], S->pq[e][1], S->pq[e][2]};
@@ -1426,6 +1433,9 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
             for (int r = 0; r < SPL; ++r)
                 if ((alive >> r & 1) && S->kf[r * 32 + lane] == 1) kmask |= 1u << r;
         } else {
+        // The classification loops make no call on their predicates: a test that the filter
+        // leaves open is marked and resolved after the loop (tight magnitudes, exact).
+        unsigned open2a = 0;   // rounds whose tetrahedron test the loose filter left open
 #pragma unroll
         for (int r = 0; r < SPL; ++r) {
             if (r >= nrounds) break;
@@ -1440,23 +1450,36 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                     // sum_k a_k^2 + w a_3^2 <= max(1, w) (sum_k a_k)^2 (loose), then the magnitudes
                     if constexpr (LOOSE) P.a = fmax((R)1, wi.a) * Vs[r] * Vs[r] * (R)1.000001;
                     else P.a = Va[r][0] * Va[r][0] + Va[r][1] * Va[r][1] + Va[r][2] * Va[r][2] + wi.a * Va[r][3] * Va[r][3];
-                    int sg = fa_sign(P, Gam<R>::g, Gam<R>::tiny);
-                    if (LOOSE && sg == 0) {
-                        const VtxFA<R> q = vertex_fa(S, v);
-                        P.a = q.a[0] * q.a[0] + q.a[1] * q.a[1] + q.a[2] * q.a[2] + wi.a * q.a[3] * q.a[3];
-                        sg = fa_sign(P, Gam<R>::g, Gam<R>::tiny);
-                    }
-                    if (sg == 0) sg = resolve_exact(c, PK_TET, S->pg[v.x], S->pg[v.y], S->pg[v.z], 0, Gam<R>::try64);
-                    f = sg <= 0 ? 1 : 0;
+                    const int sg = fa_sign(P, Gam<R>::g, Gam<R>::tiny);
+                    if (sg == 0) open2a |= 1u << r;
+                    f = sg < 0 ? 1 : 0;
                     if (f) kmask |= 1u << r;
                 }
             }
             S->kf[t] = f;
             S->tf[t] = 0;
         }
+        if (__any_sync(FULL, open2a != 0)) {
+            for (int r = 0; r < nrounds; ++r) {
+                if (!(open2a >> r & 1)) continue;
+                const int t = r * 32 + lane;
+                const uchar4 v = S->tv[t];
+                const VtxFA<R> q = vertex_fa(S, v);
+                FA<R> P;
+                P.v = q.v[0] * q.v[0] + q.v[1] * q.v[1] + q.v[2] * q.v[2] - wi.v * q.v[3] * q.v[3];
+                P.a = q.a[0] * q.a[0] + q.a[1] * q.a[1] + q.a[2] * q.a[2] + wi.a * q.a[3] * q.a[3];
+                int sg = fa_sign(P, Gam<R>::g, Gam<R>::tiny);
+                if (sg == 0) sg = resolve_exact(c, PK_TET, S->pg[v.x], S->pg[v.y], S->pg[v.z], 0, Gam<R>::try64);
+                if (sg <= 0) {
+                    S->kf[t] = 1;
+                    kmask |= 1u << r;
+                }
+            }
+        }
         __syncwarp();
 
         // ---------------- Step 2b: triangles of C (cell edges meeting B_i)
+        unsigned open2b = 0;   // (round, edge) pairs whose filters left a sign open: bit 3 r + k
 #pragma unroll
         for (int r = 0; r < SPL; ++r) {
             if (r >= nrounds) break;
@@ -1471,16 +1494,46 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                 uchar4 w = S->tv[t2];
                 uint8_t d = (w.x != a && w.x != b) ? w.x : ((w.y != a && w.y != b) ? w.y : w.z);
                 bool inK = S->kf[t] == 1 || S->kf[t2] == 1;
-                if (!inK && psign<PK_TRI>(S, c, wi, a, b) <= 0) {
-                    bool unatt = (cc < NG || psign<PK_TRIB>(S, c, wi, a, b, cc) <= 0) &&
-                                 (d < NG || psign<PK_TRIB>(S, c, wi, a, b, d) <= 0);
-                    inK = unatt;
+                if (!inK) {
+                    // psi of (i, a, b) <= 0 and no attaching plane (cc, d): filters only
+                    const int s1 = fsign<PK_TRI>(S, wi, a, b);
+                    if (s1 == 0) { open2b |= 1u << (3 * r + k); continue; }
+                    if (s1 < 0) {
+                        const int s2 = cc < NG ? -1 : fsign<PK_TRIB>(S, wi, a, b, cc);
+                        if (s2 == 0) { open2b |= 1u << (3 * r + k); continue; }
+                        if (s2 < 0) {
+                            const int s3 = d < NG ? -1 : fsign<PK_TRIB>(S, wi, a, b, d);
+                            if (s3 == 0) { open2b |= 1u << (3 * r + k); continue; }
+                            inK = s3 < 0;
+                        }
+                    }
                 }
                 if (inK) {
                     uchar4 adj2 = S->ta[t2];
                     int k2 = adj2.x == t ? 0 : (adj2.y == t ? 1 : 2);
                     atomicOr(&S->tf[t], (1u << k) | (16u << k));
                     atomicOr(&S->tf[t2], 1u << k2);
+                }
+            }
+        }
+        if (__any_sync(FULL, open2b != 0)) {
+            // the edges whose filters left a sign open, with exact predicates
+            for (int r = 0; r < nrounds; ++r) {
+                for (int k = 0; k < 3; ++k) {
+                    if (!(open2b >> (3 * r + k) & 1)) continue;
+                    const int t = r * 32 + lane;
+                    const uchar4 v = S->tv[t];
+                    const int t2 = tv_get(S->ta[t], k) & (NT - 1);
+                    const uint8_t a = tv_get(v, k), b = tv_get(v, (k + 1) % 3), cc = tv_get(v, (k + 2) % 3);
+                    const uchar4 w = S->tv[t2];
+                    const uint8_t d = (w.x != a && w.x != b) ? w.x : ((w.y != a && w.y != b) ? w.y : w.z);
+                    if (psign<PK_TRI>(S, c, wi, a, b) <= 0 && (cc < NG || psign<PK_TRIB>(S, c, wi, a, b, cc) <= 0) &&
+                        (d < NG || psign<PK_TRIB>(S, c, wi, a, b, d) <= 0)) {
+                        const uchar4 adj2 = S->ta[t2];
+                        const int k2 = adj2.x == t ? 0 : (adj2.y == t ? 1 : 2);
+                        atomicOr(&S->tf[t], (1u << k) | (16u << k));
+                        atomicOr(&S->tf[t2], 1u << k2);
+                    }
                 }
             }
         }
@@ -1545,7 +1598,11 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
             }
         };
         if constexpr (PH != PH_TERMS) {
-        for (int a = NG + lane; a < NG + nc; a += 32) {
+        // faces whose edge test the filters left open (bit = the lane's face iteration), and
+        // which of them are closed; resolved after the loop (the fused kernel decides in place)
+        unsigned open2c = 0, closed2c = 0;
+        int it2c = 0;
+        for (int a = NG + lane; a < NG + nc; a += 32, ++it2c) {
             uint8_t flag = 0;
             R phi_sum = zero;
             int st = S->start[a];
@@ -1584,18 +1641,46 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                 }
                 bool closed = (nk == nv) && !ghost;
                 bool eK = triK;
-                if (!eK && psign<PK_EDGE>(S, c, wi, a, 0) <= 0) {
-                    // is the edge orthocentre inside the face polygon?  walk again over its sides
-                    t = st & (NT - 1);
-                    for (int step = 0; step < NT && inside; ++step) {
-                        uchar4 v = S->tv[t];
-                        int k = v.x == a ? 0 : (v.y == a ? 1 : 2);
-                        uint8_t b = tv_get(v, (k + 1) % 3);
-                        if (b >= NG && psign<PK_EDGEB>(S, c, wi, a, b) > 0) inside = false;
-                        t = tv_get(S->ta[t], k) & (NT - 1);
-                        if (t == (st & (NT - 1))) break;
+                if constexpr (PH == PH_ALL) {
+                    if (!eK && psign<PK_EDGE>(S, c, wi, a, 0) <= 0) {
+                        // is the edge orthocentre inside the face polygon?  walk again over its sides
+                        t = st & (NT - 1);
+                        for (int step = 0; step < NT && inside; ++step) {
+                            uchar4 v = S->tv[t];
+                            int k = v.x == a ? 0 : (v.y == a ? 1 : 2);
+                            uint8_t b = tv_get(v, (k + 1) % 3);
+                            if (b >= NG && psign<PK_EDGEB>(S, c, wi, a, b) > 0) inside = false;
+                            t = tv_get(S->ta[t], k) & (NT - 1);
+                            if (t == (st & (NT - 1))) break;
+                        }
+                        eK = inside;
                     }
-                    eK = inside;
+                } else if (!eK) {
+                    // the same tests with the filters only; an open one defers the face
+                    const int se = fsign<PK_EDGE>(S, wi, a, a);
+                    bool open = se == 0;
+                    if (se < 0) {
+                        bool out = false;
+                        t = st & (NT - 1);
+                        for (int step = 0; step < NT; ++step) {
+                            uchar4 v = S->tv[t];
+                            int k = v.x == a ? 0 : (v.y == a ? 1 : 2);
+                            uint8_t b = tv_get(v, (k + 1) % 3);
+                            if (b >= NG) {
+                                const int sb = fsign<PK_EDGEB>(S, wi, a, b);
+                                if (sb > 0) { out = true; break; }
+                                if (sb == 0) open = true;
+                            }
+                            t = tv_get(S->ta[t], k) & (NT - 1);
+                            if (t == (st & (NT - 1))) break;
+                        }
+                        if (out) open = false;
+                        else if (!open) eK = true;
+                    }
+                    if (open) {
+                        open2c |= 1u << it2c;
+                        if (closed) closed2c |= 1u << it2c;
+                    }
                 }
                 if (eK) {
                     flag = 1 | (closed ? 2 : 0);
@@ -1605,6 +1690,31 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                 }
             }
             S->eflag[a] = flag;
+        }
+        if (PH != PH_ALL && __any_sync(FULL, open2c != 0)) {
+            // the deferred faces, with exact predicates
+            it2c = 0;
+            for (int a = NG + lane; a < NG + nc; a += 32, ++it2c) {
+                if (!(open2c >> it2c & 1)) continue;
+                const int st = S->start[a] & (NT - 1);
+                bool eK = false;
+                if (psign<PK_EDGE>(S, c, wi, a, 0) <= 0) {
+                    eK = true;
+                    int t = st;
+                    for (int step = 0; step < NT; ++step) {
+                        const uchar4 v = S->tv[t];
+                        const int k = v.x == a ? 0 : (v.y == a ? 1 : 2);
+                        const uint8_t b = tv_get(v, (k + 1) % 3);
+                        if (b >= NG && psign<PK_EDGEB>(S, c, wi, a, b) > 0) { eK = false; break; }
+                        t = tv_get(S->ta[t], k) & (NT - 1);
+                        if (t == st) break;
+                    }
+                }
+                if (eK) {
+                    S->eflag[a] = 1 | ((closed2c >> it2c & 1) ? 2 : 0);
+                    myEK = 1;
+                }
+            }
         }
         __syncwarp();
         } else {
@@ -1622,8 +1732,8 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                 int k = v.x == a ? 0 : (v.y == a ? 1 : 2);
                 if (S->kf[t] == 1) {
                     P3<R> pb = ppos(S, tv_get(v, (k + 1) % 3)), pc = ppos(S, tv_get(v, (k + 2) % 3));
-                    phi_sum += dihedral_ol(O, pa, pb, pc);
-                    if (GRAD) gsum = gsum + dihedral_grad_u_ol(O, pa, pb, pc, (R)1);
+                    phi_sum += dihedral(O, pa, pb, pc);
+                    if (GRAD) gsum = gsum + dihedral_grad_u_in(O, pa, pb, pc, (R)1);
                 }
                 t = tv_get(S->ta[t], k) & (NT - 1);
                 if (t == st) break;
@@ -1709,7 +1819,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
             for (int r = 0; r < SPL; ++r) {
                 if (!(kmask >> r & 1)) continue;
                 uchar4 v = S->tv[r * 32 + lane];
-                om += solid_angle_half_ol(ppos(S, v.x), ppos(S, v.y), ppos(S, v.z));
+                om += solid_angle_half(ppos(S, v.x), ppos(S, v.y), ppos(S, v.z));
             }
             if constexpr (FFM) {
                 // - 2 R_i^2 (half solid angles) in float-float; the 4 pi R_i^2 is added once below
@@ -1763,7 +1873,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                     const float2 ra2 = A.Rhl[ga], rb2 = A.Rhl[gb];
                     const FF Ra = {ra2.x, ra2.y}, Rb = {rb2.x, rb2.y};
                     if (part == 3) {
-                        FF v = tri_term_ff_ol(pa, pb, Ri_ff, Ra, Rb, Ri2_ff, -1.f);
+                        FF v = tri_term_ff(pa, pb, Ri_ff, Ra, Rb, Ri2_ff, -1.f);
                         acc_ff = ff_add(acc_ff, FF{cff * v.h, cff * v.l});
                         cf_sum += cff;
                     }
@@ -1787,7 +1897,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                     const R r0 = part == 0 ? Rr : (part == 1 ? Raf : Rbf);
                     const R r1 = part == 0 ? Raf : Rr;
                     const R r2 = part == 2 ? Raf : Rbf;
-                    P3x2f<R> lg = lens_grad_ol(u, w, r0, r1, r2, (R)-1);
+                    P3x2f<R> lg = lens_grad_in(u, w, r0, r1, r2, (R)-1);
                     if (FFM && lg.refine) {
                         // The lens gradient is linear in the height s_t of the triple points over
                         // the plane of the centres, whose float value (R^2 - |z|^2) errs by about
@@ -1799,7 +1909,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                         const P3<double> qa = {A.xyz[3 * ga] - c.pi[0], A.xyz[3 * ga + 1] - c.pi[1], A.xyz[3 * ga + 2] - c.pi[2]};
                         const P3<double> qb = {A.xyz[3 * gb] - c.pi[0], A.xyz[3 * gb + 1] - c.pi[1], A.xyz[3 * gb + 2] - c.pi[2]};
                         const float s2 = triple_height2_gram(qa, qb, c.Ri, A.R[ga], A.R[gb]);
-                        lg = lens_grad_ol(u, w, r0, r1, r2, (R)(s2 > 0.f ? sqrtf(s2) : 0.f));
+                        lg = lens_grad_in(u, w, r0, r1, r2, (R)(s2 > 0.f ? sqrtf(s2) : 0.f));
                     }
                     const R f = cff * (part == 0 ? -wif : (part == 1 ? waf : wbf));
                     R sx = f * (part == 0 ? lg.a.x + lg.b.x : lg.a.x);
@@ -1815,7 +1925,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                         const R dab = norm3(pb - pa), inv2 = (R)0.5 / dab;
                         const R tab = (dab * dab + dRab) * inv2, tba = (dab * dab - dRab) * inv2;
                         const R kap = -(waf * Raf * tab + wbf * Rbf * tba);
-                        P3<R> gc = dihedral_grad_c_ol(pa, pb, O, ppos(S, x), on_t ? (R)1 : (R)-1);
+                        P3<R> gc = dihedral_grad_c_in(pa, pb, O, ppos(S, x), on_t ? (R)1 : (R)-1);
                         sx += kap * gc.x; sy += kap * gc.y; sz += kap * gc.z;
                     }
                     gacc.add(sx, sy, sz);

@@ -714,29 +714,30 @@ template <class T> DS_HD void tri_disk_moment(T ax, T ay, T bx, T by, T r, T& mx
 }
 
 // ------------------------------------------------------------------ out-of-line forms
-// The kernels call the heavy terms through these (one copy of each body instead of one per
-// call site), which keeps the kernels small enough for the instruction cache.  Results are
-// returned by value so that no caller variable has to live in local memory.
+// The kernels call the heavy terms through these where code size matters more (one copy of
+// each body instead of one per call site); results are returned by value so that no caller
+// variable has to live in local memory.  A call inside a hot loop costs more than the code
+// (the loop's state is kept across it), so the terms kernel's loops use the inline forms
+// (_in) and keep calls for rare paths.
 template <class T> struct P3x2 { P3<T> a, b; };
 template <class T> DS_HDC T dihedral_ol(P3<T> u, P3<T> v, P3<T> c, P3<T> d) { return dihedral(u, v, c, d); }
 // d theta / d u of dihedral_grad_s
-template <class T> DS_HDC P3<T> dihedral_grad_u_ol(P3<T> u, P3<T> v, P3<T> c, P3<T> d, T sg) {
+template <class T> DS_HD P3<T> dihedral_grad_u_in(P3<T> u, P3<T> v, P3<T> c, P3<T> d, T sg) {
     P3<T> gu, gv, gc, gd;
     dihedral_grad_s(u, v, c, d, sg, gu, gv, gc, gd);
     return gu;
 }
+template <class T> DS_HDC P3<T> dihedral_grad_u_ol(P3<T> u, P3<T> v, P3<T> c, P3<T> d, T sg) {
+    return dihedral_grad_u_in(u, v, c, d, sg);
+}
 // d theta / d c of dihedral_grad_s
-template <class T> DS_HDC P3<T> dihedral_grad_c_ol(P3<T> u, P3<T> v, P3<T> c, P3<T> d, T sg) {
+template <class T> DS_HD P3<T> dihedral_grad_c_in(P3<T> u, P3<T> v, P3<T> c, P3<T> d, T sg) {
     P3<T> gu, gv, gc, gd;
     dihedral_grad_s(u, v, c, d, sg, gu, gv, gc, gd);
     return gc;
 }
-template <class T> DS_HDC T solid_angle_half_ol(P3<T> a, P3<T> b, P3<T> c) { return solid_angle_half(a, b, c); }
 template <class T> DS_HDC double tri_term_mixed_ol(P3<T> p2, P3<T> p3, double R1, double R2, double R3) {
     return tri_term_mixed(p2, p3, R1, R2, R3);
-}
-static DS_HDC FF tri_term_ff_ol(P3<float> p2, P3<float> p3, FF R1, FF R2, FF R3, FF R1sq, float s_ext) {
-    return tri_term_ff(p2, p3, R1, R2, R3, R1sq, s_ext);
 }
 template <class T> DS_HDC T tri_disk_area_ol(T ax, T ay, T bx, T by, T r) { return tri_disk_area(ax, ay, bx, by, r); }
 template <class T> struct T2 { T x, y; };
@@ -746,7 +747,7 @@ template <class T> DS_HDC T2<T> tri_disk_moment_ol(T ax, T ay, T bx, T by, T r) 
     return m;
 }
 template <class T> struct P3x2f { P3<T> a, b; bool refine; };
-template <class T> DS_HDC P3x2f<T> lens_grad_ol(P3<T> q2, P3<T> q3, T R1, T R2, T R3, T st_ext) {
+template <class T> DS_HD P3x2f<T> lens_grad_in(P3<T> q2, P3<T> q3, T R1, T R2, T R3, T st_ext) {
     P3x2f<T> r;
     r.refine = lens_grad(q2, q3, R1, R2, R3, r.a, r.b, st_ext);
     return r;
@@ -756,7 +757,7 @@ template <class T> DS_HDC P3x2f<T> lens_grad_ol(P3<T> q2, P3<T> q3, T R1, T R2, 
 // |z|^2 = (b2^2 G33 - 2 b2 b3 G23 + b3^2 G22) / det G and
 // s^2 = (R1^2 det G - b2^2 G33 + 2 b2 b3 G23 - b3^2 G22) / det G; the cancellation happens in
 // the float64 numerator, and the division is taken in float.
-static DS_HDC float triple_height2_gram(P3<double> q2, P3<double> q3, double R1, double R2, double R3) {
+static DS_HD float triple_height2_gram(P3<double> q2, P3<double> q3, double R1, double R2, double R3) {
     const double g22 = dot3(q2, q2), g33 = dot3(q3, q3), g23 = dot3(q2, q3);
     const double R1s = R1 * R1;
     const double b2 = 0.5 * ((g22 - R2 * R2) + R1s), b3 = 0.5 * ((g33 - R3 * R3) + R1s);

@@ -44,6 +44,15 @@ def _check_against_oracle(orc, rec, x, r):
         assert who == set(simp), (simp, who)
 
 
+def _grad_close(g, ref):
+    """The mixed form's gradient bound: 1e-3 relative, and its measured rounding floor of
+    3e-5 absolute where |g| < 0.03."""
+    err = np.linalg.norm(g - ref, axis=1)
+    tol = np.maximum(1e-3 * np.linalg.norm(ref, axis=1), 3e-5)
+    bad = np.nonzero(err > tol)[0]
+    assert len(bad) == 0, (bad[:5], err[bad[:5]], np.linalg.norm(ref, axis=1)[bad[:5]])
+
+
 def _run(torch, ctx, x, r, weights=None):
     n = len(r)
     a = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -102,13 +111,11 @@ def test_carry_matches_fresh_cells(api, torch_cuda, orc, gen):
         for aa, gg in ((a, g), (ap, gp)):
             assert np.all(np.abs(aa - af) <= 1e-5 * np.maximum(af, 1.0))
             assert abs(aa.sum() - af.sum()) <= 1e-8 * af.sum()
-            err = np.linalg.norm(gg - gf, axis=1)
-            assert np.all(err <= 1e-3 * np.maximum(np.linalg.norm(gf, axis=1), 1e-2))
+            _grad_close(gg, gf)
     ra, _, rg = orc.sasa(x, m.radii)
     assert np.all(np.abs(a - ra) <= 1e-4 * np.maximum(ra, 1.0))
     assert abs(a.sum() - ra.sum()) <= 1e-6 * ra.sum()
-    err = np.linalg.norm(g - rg, axis=1)
-    assert np.all(err <= 1e-3 * np.maximum(np.linalg.norm(rg, axis=1), 1e-2))
+    _grad_close(g, rg)
     for c in (carry, plain, fresh):
         c.close()
 
