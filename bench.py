@@ -470,7 +470,7 @@ def trajectory_measure(args, local):
     m = inputs.make("globule", 20000, 0)
     dev = torch.device("cuda", local)
     out = {"workload": "graphed trajectory, 20,000-atom globule, sigma 0.01 A"}
-    for name, skin, carry in (("skin_0", 0.0, False), ("skin_1", 1.0, False), ("skin_1_carry", 1.0, True)):
+    for name, skin, carry in (("skin_0", 0.0, 0), ("skin_1", 1.0, 0), ("skin_1_carry", 1.0, 1)):
         tr = ag.GraphedTrajectory(torch.as_tensor(m.coords, device=dev), torch.as_tensor(m.radii, device=dev),
                                   sigma=0.01, seed=0, skin=skin, carry=carry).capture()
         tr.replay(args.warmup)

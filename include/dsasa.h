@@ -55,7 +55,10 @@ typedef enum {
                                     (coincident atoms); exact ties of co-spherical or
                                     co-planar atoms are broken as the regular triangulation
                                     breaks them and are not errors */
-    DSASA_ERR_INPUT = 8          /* non-finite coordinate or radius found on the device */
+    DSASA_ERR_INPUT = 8,         /* non-finite coordinate or radius found on the device */
+    DSASA_ERR_CHECK = 9          /* the checked build (compiled with DSASA_CHECKED) found an
+                                    index out of its array on the device; the access was
+                                    redirected inside the array and the call's results are void */
 } dsasa_status;
 
 /* Precision of the arithmetic (the predicates that decide which simplices exist are exact
@@ -90,16 +93,18 @@ typedef struct {
                          * rounding. */
     int64_t max_atoms;  /* fixed capacity in atoms, or 0 to grow on demand */
     int64_t max_cells;  /* cap on cell-list cells (0 = default 2^22); larger boxes use coarser cells */
-    int carry;          /* with skin > 0: on calls that reuse the lists, start each atom's cell
-                         * from the one the previous call built (its faces' planes at the current
-                         * positions), kept when exact predicates certify it and then cut by the
-                         * new neighbours; else built afresh.  The incremental update of the
-                         * complex across MD steps of the paper's Conclusions.  Results equal a
-                         * fresh build's up to the rounding of the terms (the simplices of the
-                         * complex are the same).  Default 1. */
+    int carry;          /* with skin > 0, on calls that reuse the lists: keep each atom's cell
+                         * from the previous call (its faces' planes at the current positions)
+                         * when exact predicates certify that it is still the cell and no new
+                         * neighbour cuts it; the other cells are built afresh.  The incremental
+                         * update of the complex across MD steps (the paper's Conclusions).  The
+                         * simplices of the complex are the same as a fresh build's, the areas
+                         * and gradient equal up to the rounding of the terms.  0: off; 1
+                         * (default): for molecules of more than one wave of the fused cell
+                         * kernel (about 5,400 atoms on a GB300), where it pays; 2: always. */
 } dsasa_config;
 
-/* Fills cfg with defaults: MIXED, skin 0, grow on demand, default cell cap, carry 1. */
+/* Fills cfg with defaults: MIXED, skin 0, grow on demand, default cell cap, carry 1 (auto). */
 void dsasa_default_config(dsasa_config* cfg);
 
 /* Creates a context on `device` (CUDA ordinal) bound to `cuda_stream` (a cudaStream_t, or

@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 DSASA_OK = 0
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CAPACITY", 4: "ERR_UNRESOLVED", 5: "ERR_CUDA",
-                6: "ERR_UNIMPLEMENTED", 7: "ERR_DEGENERATE", 8: "ERR_INPUT"}
+                6: "ERR_UNIMPLEMENTED", 7: "ERR_DEGENERATE", 8: "ERR_INPUT", 9: "ERR_CHECK"}
 DSASA_MIXED, DSASA_FP64 = 0, 1
 PROBE = 1.4
 
@@ -123,14 +123,14 @@ class Context:
     """One dsasa_ctx bound to a device and a stream (default: torch's current stream)."""
 
     def __init__(self, device: int = 0, stream=None, precision: str | int = "mixed", skin: float = 0.0,
-                 max_atoms: int = 0, max_cells: int = 0, carry: bool = True):
+                 max_atoms: int = 0, max_cells: int = 0, carry: int = 1):
         cfg = dsasa_config()
         _lib.dsasa_default_config(ctypes.byref(cfg))
         cfg.precision = precision if isinstance(precision, int) else {"mixed": DSASA_MIXED, "fp64": DSASA_FP64}[precision]
         cfg.skin = float(skin)
         cfg.max_atoms = int(max_atoms)
         cfg.max_cells = int(max_cells)
-        cfg.carry = int(bool(carry))
+        cfg.carry = int(carry)   # 0 off, 1 beyond one wave of the fused cell kernel, 2 always
         self.device = device
         h = _vp()
         st = _lib.dsasa_create(ctypes.byref(h), device, _vp(self._stream_handle(stream)), ctypes.byref(cfg))

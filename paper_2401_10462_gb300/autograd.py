@@ -129,14 +129,15 @@ class GraphedTrajectory:
     captured CUDA graph.  Capacities are fixed at construction (no allocation in the graph)."""
 
     def __init__(self, coords, radii, sigma: float = 0.01, gamma: float = GAMMA, seed: int = 0,
-                 precision: str = "mixed", headroom: float = 1.25, skin: float = 0.0, carry: bool = True):
+                 precision: str = "mixed", headroom: float = 1.25, skin: float = 0.0, carry: int = 1):
         dev = coords.device
         n = coords.shape[0]
         self.n = n
         self.stream = torch.cuda.Stream(device=dev)
         # skin > 0: the neighbour lists stay on the device between steps and are rebuilt by
         # the device itself once an atom has moved by half the skin (no host decision in the
-        # graph); with carry, steps that reuse the lists start each cell from the previous step's
+        # graph); with carry (see api.Context), steps that reuse the lists keep the previous
+        # step's cells where exact predicates certify them
         self.lib_ctx = api.Context(device=dev.index or 0, stream=self.stream, precision=precision,
                                    max_atoms=int(n * headroom) + 64, skin=skin, carry=carry)
         self.x = coords.detach().clone().contiguous()

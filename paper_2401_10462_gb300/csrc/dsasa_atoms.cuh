@@ -215,6 +215,7 @@ struct Ctx {
     double Ri;
     double h;
     int i;
+    int n;          // atoms (the range of plane owners)
     int* status;
 };
 
@@ -225,6 +226,7 @@ __device__ void plane64_of(const Ctx& c, int g, double q[3], double& b, double& 
         exact = true;
         return;
     }
+    g = DS_IDX(g, c.n, c.status);
     double pk[3] = {c.xyz[3 * g], c.xyz[3 * g + 1], c.xyz[3 * g + 2]};
     plane64(c.pi, c.Ri, pk, c.R[g], q, b, babs);
     exact = false;
@@ -237,6 +239,7 @@ __device__ PlaneN<FA<double>> fa64_of(const Ctx& c, int g) {
 }
 __device__ PlaneN<XP> xp_of(const Ctx& c, int g) {
     if (g < 0) return xp_ghost(-1 - g, c.h);
+    g = DS_IDX(g, c.n, c.status);
     double pk[3] = {c.xyz[3 * g], c.xyz[3 * g + 1], c.xyz[3 * g + 2]};
     return xp_plane(c.pi, c.Ri, pk, c.R[g]);
 }
@@ -339,8 +342,8 @@ template <class SM, class R = typename SM::Real> __device__ __noinline__ VtxFA<R
 // weighted entry is w_i (the unweighted one) + sum_f (w_i - w_k) m_f / |q_f| (wx, wy, wz).
 // Per lane: partial sums over faces.
 template <class SM, class R = typename SM::Real>
-__device__ void cell_volume_terms(const SM* S, int nc, R Ri, int lane, const double* vw, R wi, R& hs, R& nx,
-                                  R& ny, R& nz, R& wx, R& wy, R& wz) {
+__device__ void cell_volume_terms(const SM* S, int nc, R Ri, int lane, const double* vw, R wi, int n, int* status,
+                                  R& hs, R& nx, R& ny, R& nz, R& wx, R& wy, R& wz) {
     constexpr int NT = SM::kNT, NE = SM::kNE;
     hs = nx = ny = nz = wx = wy = wz = (R)0;
     for (int a = lane; a < NG + nc; a += 32) {
@@ -363,7 +366,7 @@ __device__ void cell_volume_terms(const SM* S, int nc, R Ri, int lane, const dou
         const P3<R> e2 = cross3(u, e1);
         int t = st;
         R fx = 0, fy = 0, px = 0, py = 0, sin_ = 0, sout = 0, m1 = 0, m2 = 0;
-        const int gk = S->pg[a];
+        const int gk = S->pg[a];   // < 0: a ghost plane
         const bool moments = vw != nullptr && gk >= 0 && r > (R)0;
         auto fan = [&](R ax, R ay, R bx, R by) {
             const R full = (R)0.5 * (ax * by - ay * bx);
@@ -407,7 +410,7 @@ __device__ void cell_volume_terms(const SM* S, int nc, R Ri, int lane, const dou
         nz += sout * sg * u.z;
         if (moments) {
             // m_f = s_f (h u) + m1 e1 + m2 e2, scaled by (w_i - w_k) / |q_f|
-            const R f = (wi - (R)vw[gk]) * inv * sg;
+            const R f = (wi - (R)vw[DS_IDX(gk, n, status)]) * inv * sg;
             wx += f * (sin_ * h * u.x + m1 * e1.x + m2 * e2.x);
             wy += f * (sin_ * h * u.y + m1 * e1.y + m2 * e2.y);
             wz += f * (sin_ * h * u.z + m1 * e1.z + m2 * e2.z);
@@ -667,8 +670,8 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
     const int total = deferred ? *A.work_count : A.n;
 
     for (int s0 = blockIdx.x * WARPS + wib; s0 < total; s0 += nwarps) {
-        const int s = deferred ? A.work_list[s0] : s0;
-        const int i = A.sidx[s];
+        const int s = DS_IDX(deferred ? A.work_list[s0] : s0, A.n, A.status);
+        const int i = DS_IDX(A.sidx[s], A.n, A.status);
         const float4 fi = A.sf4[s];
         const MolGrid G = A.grids[A.molid[i]];
         Ctx c;
@@ -680,6 +683,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
         c.Ri = A.R[i];
         c.h = ghost_h(c.Ri);
         c.i = i;
+        c.n = A.n;
         c.status = A.status;
         const R Rr = (R)c.Ri;
         const FA<R> wi = {Rr * Rr, Rr * Rr};
@@ -692,7 +696,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
         };
         // PH_CARRY: this atom's cell is built by the cell kernel that follows, from the redo list
         auto redo = [&]() {
-            if (lane == 0) A.redo_list[atomicAdd(A.redo_count, 1)] = s;
+            if (lane == 0) A.redo_list[DS_IDX(atomicAdd(A.redo_count, 1), A.n, A.status)] = s;
             __syncwarp();
         };
         // the outputs of this atom are final (lane 0 wrote them): count it for its molecule
@@ -728,7 +732,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
         auto write_volume = [&](double Ai) {
             R hs, nx, ny, nz, wx, wy, wz;
             const double wv = A.vw ? A.vw[i] : 1.0;
-            cell_volume_terms(S, nc, Rr, lane, A.vgrad ? A.vw : nullptr, (R)wv, hs, nx, ny, nz, wx, wy, wz);
+            cell_volume_terms(S, nc, Rr, lane, A.vgrad ? A.vw : nullptr, (R)wv, A.n, A.status, hs, nx, ny, nz, wx, wy, wz);
             const double hsum = warp_sum_d((double)hs);
             const double gx = warp_sum_d((double)nx), gy = warp_sum_d((double)ny), gz = warp_sum_d((double)nz);
             double ex = 0.0, ey = 0.0, ez = 0.0;
@@ -762,7 +766,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                 bool ok = false;
                 int j = -1;
                 if (k < nl) {
-                    j = A.nbl[li * NBL_CAP + k] + lofs;
+                    j = DS_IDX(A.nbl[li * NBL_CAP + k] + lofs, A.n, A.status);
                     const double dx = A.xyz[3 * j] - c.pi[0], dy = A.xyz[3 * j + 1] - c.pi[1], dz = A.xyz[3 * j + 2] - c.pi[2];
                     const double rr = c.Ri + A.R[j];
                     ok = dx * dx + dy * dy + dz * dz < rr * rr * (1.0 + 1e-9);
@@ -791,7 +795,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                         int j = -1;
                         if (k < end) {
                             float4 fj = A.sf4[k];
-                            j = A.sidx[k];
+                            j = DS_IDX(A.sidx[k], A.n, A.status);
                             float dx = fj.x - fi.x, dy2 = fj.y - fi.y, dz2 = fj.z - fi.z;
                             float rr = fi.w + fj.w + G.margin;
                             ok = (j != i) && (dx * dx + dy2 * dy2 + dz2 * dz2 < rr * rr);
@@ -862,7 +866,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
             if (nc > KMAX) { redo(); continue; }
         }
         if (nc > KMAX && can_defer) {
-            if (lane == 0) A.defer_list[atomicAdd(A.defer_count, 1)] = s;
+            if (lane == 0) A.defer_list[DS_IDX(atomicAdd(A.defer_count, 1), A.n, A.status)] = s;
             no_cell();
             done();
             __syncwarp();
@@ -1268,7 +1272,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
         __syncwarp();
         const bool bad = S->bad != 0;
         if (bad && S->bad == 2 && can_defer) {
-            if (lane == 0) A.defer_list[atomicAdd(A.defer_count, 1)] = s;
+            if (lane == 0) A.defer_list[DS_IDX(atomicAdd(A.defer_count, 1), A.n, A.status)] = s;
             no_cell();
             done();
             __syncwarp();
@@ -1568,7 +1572,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
             // edge term of A_i (Eqs. phiedge, edge): - Phi_ia S_ia^(i) with
             // S_ia^(i) = 2 pi R_i h_i and Phi_ia = 1 - sum(theta) / 2 pi, i.e.
             // R_i h_i (sum(theta) - 2 pi); h_i = (R_i + R_a - d)(R_a - R_i + d) / 2d
-            int ga = S->pg[a];
+            int ga = DS_IDX(S->pg[a], A.n, A.status);
             const R dr = norm3(pa), inv2d = (R)0.5 / dr;
             R Raf, dR2;
             if constexpr (FFM) {
@@ -1867,7 +1871,7 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
                 int nk = (S->kf[t] == 1) + (S->kf[t2] == 1);
                 const R cff = (R)1 - (R)0.5 * (R)nk;
                 P3<R> pa = ppos(S, a), pb = ppos(S, b);
-                int ga = S->pg[a], gb = S->pg[b];
+                int ga = DS_IDX(S->pg[a], A.n, A.status), gb = DS_IDX(S->pg[b], A.n, A.status);
                 R Raf, Rbf, dRab;
                 if constexpr (FFM) {
                     const float2 ra2 = A.Rhl[ga], rb2 = A.Rhl[gb];
@@ -2058,7 +2062,7 @@ cudaError_t launch_atoms_t(const AtomArgs& a, bool grad, cudaStream_t s) {
     };
     if (a.cells) {
         auto nb = [&](int w) { return (a.n + w - 1) / w; };
-        if (cells_in_one_wave<R>(a.n) && !a.carry) {
+        if (!a.carry && cells_in_one_wave<R>(a.n)) {
             go(k_atoms<R, false, 64, 64, PH_CC>, nb(WARPS_CELL), WARPS_CELL * 32, fast);
             mark(0);
             mark(1);

@@ -4,6 +4,7 @@
 #include "dsasa_kernels.cuh"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -267,7 +268,12 @@ dsasa_status run(dsasa_ctx* c, const double* coords, const double* radii, double
         a.radii_in = radii;
     }
     a.skin_band = c->cfg.skin > 0.0;
-    a.carry = lists && c->cfg.carry != 0;
+    // carried cells: always (carry 2), or (carry 1) for molecules of more than one wave of the
+    // fused cell kernel, where they pay (within one wave the fused kernel is faster)
+    if (lists && c->cfg.carry != 0) {
+        const bool one_wave = c->cfg.precision == DSASA_FP64 ? atoms_one_wave_f64((int)n) : atoms_one_wave_f32((int)n);
+        a.carry = c->cfg.carry == 2 || !one_wave;
+    }
     a.redo_list = c->redo;
     a.redo_count = c->status + 3;   // cleared by the cell-list build
     a.mol_off = offsets_dev;
@@ -309,6 +315,15 @@ dsasa_status check_common(dsasa_ctx* c, const double* coords, const double* radi
 
 }  // namespace
 
+// NVTX range over one entry point (host side: argument checks, allocation, enqueue), visible
+// in a profiler's timeline next to the kernels it launched; free when no tool is attached
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 extern "C" {
 
 void dsasa_default_config(dsasa_config* cfg) {
@@ -329,6 +344,7 @@ dsasa_status dsasa_create(dsasa_ctx** out, int device, void* cuda_stream, const 
     if (!c) return DSASA_ERR_OOM;
     if (cfg) c->cfg = *cfg; else dsasa_default_config(&c->cfg);
     if ((c->cfg.precision != DSASA_MIXED && c->cfg.precision != DSASA_FP64) || !(c->cfg.skin >= 0.0) ||
+        c->cfg.carry < 0 || c->cfg.carry > 2 ||
         c->cfg.max_atoms < 0 || c->cfg.max_cells < 0) {
         delete c;
         return DSASA_ERR_ARG;
@@ -371,6 +387,7 @@ dsasa_status dsasa_set_precision(dsasa_ctx* c, int precision) {
 
 dsasa_status dsasa_compute_vjp(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
                                const double* area_weights, double* areas_out, double* grad_out) {
+    NvtxRange nvtx_range("dsasa_compute_vjp");
     dsasa_status st = check_common(c, coords, radii, probe, n, areas_out);
     if (st != DSASA_OK || n == 0) return st;
     return run(c, coords, radii, probe, n, 1, nullptr, area_weights, areas_out, grad_out, nullptr, 0);
@@ -378,11 +395,13 @@ dsasa_status dsasa_compute_vjp(dsasa_ctx* c, const double* coords, const double*
 
 dsasa_status dsasa_compute(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
                            double* areas_out, double* grad_out) {
+    NvtxRange nvtx_range("dsasa_compute");
     return dsasa_compute_vjp(c, coords, radii, probe, n, nullptr, areas_out, grad_out);
 }
 
 dsasa_status dsasa_compute_volume(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
                                   double* areas_out, double* grad_out, double* volumes_out, double* vol_grad_out) {
+    NvtxRange nvtx_range("dsasa_compute_volume");
     dsasa_status st = check_common(c, coords, radii, probe, n, areas_out);
     if (st != DSASA_OK || n == 0) return st;
     if (!volumes_out) return fail(c, DSASA_ERR_ARG, "volumes_out is NULL");
@@ -393,6 +412,7 @@ dsasa_status dsasa_compute_volume(dsasa_ctx* c, const double* coords, const doub
 dsasa_status dsasa_compute_volume_vjp(dsasa_ctx* c, const double* coords, const double* radii, double probe,
                                       int64_t n, const double* volume_weights, double* areas_out, double* volumes_out,
                                       double* vol_grad_out) {
+    NvtxRange nvtx_range("dsasa_compute_volume_vjp");
     dsasa_status st = check_common(c, coords, radii, probe, n, areas_out);
     if (st != DSASA_OK || n == 0) return st;
     if (!volumes_out || !vol_grad_out) return fail(c, DSASA_ERR_ARG, "volumes_out and vol_grad_out are required");
@@ -402,6 +422,7 @@ dsasa_status dsasa_compute_volume_vjp(dsasa_ctx* c, const double* coords, const 
 
 dsasa_status dsasa_compute_sr(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
                               const float* unit_points, int m, double* areas_out, int32_t* exposed_out) {
+    NvtxRange nvtx_range("dsasa_compute_sr");
     dsasa_status st = check_common(c, coords, radii, probe, n, areas_out);
     if (st != DSASA_OK || n == 0) return st;
     if (!unit_points || m <= 0) return fail(c, DSASA_ERR_ARG, "need m > 0 unit points");
@@ -470,6 +491,7 @@ dsasa_status dsasa_sr_tests(dsasa_ctx* c, int64_t* tests) {
 dsasa_status dsasa_compute_batch(dsasa_ctx* c, int n_mol, const int64_t* atom_offsets, const double* coords,
                                  const double* radii, double probe, const double* area_weights, double* areas_out,
                                  double* grad_out) {
+    NvtxRange nvtx_range("dsasa_compute_batch");
     if (!c) return DSASA_ERR_ARG;
     if (n_mol < 0 || (n_mol > 0 && !atom_offsets)) return fail(c, DSASA_ERR_ARG, "invalid molecule offsets");
     if (n_mol == 0) return DSASA_OK;
@@ -532,6 +554,7 @@ dsasa_status dsasa_compute_batch_resident(dsasa_ctx* c, dsasa_arena* arena, int 
                                           const int64_t* arena_base, const double* coords, const double* radii,
                                           double probe, const double* area_weights, double* areas_out,
                                           double* grad_out, int32_t* mol_ready) {
+    NvtxRange nvtx_range("dsasa_compute_batch_resident");
     if (!c) return DSASA_ERR_ARG;
     if (n_mol < 0 || (n_mol > 0 && !atom_offsets)) return fail(c, DSASA_ERR_ARG, "invalid molecule offsets");
     if (n_mol == 0) return DSASA_OK;
@@ -581,6 +604,7 @@ dsasa_status dsasa_batch_reused(dsasa_ctx* c, int n_mol, int32_t* reused_host) {
 
 dsasa_status dsasa_compute_host(dsasa_ctx* c, const double* coords_host, const double* radii_host, double probe,
                                 int64_t n, const double* weights_host, double* areas_host, double* grad_host) {
+    NvtxRange nvtx_range("dsasa_compute_host");
     dsasa_status st = check_common(c, coords_host, radii_host, probe, n, areas_host);
     if (st != DSASA_OK || n == 0) return st;
     cudaError_t e;
@@ -615,6 +639,7 @@ dsasa_status dsasa_compute_host(dsasa_ctx* c, const double* coords_host, const d
 }
 
 dsasa_status dsasa_status_sync(dsasa_ctx* c) {
+    NvtxRange nvtx_range("dsasa_status_sync");
     if (!c) return DSASA_ERR_ARG;
     cudaError_t e = cudaSetDevice(c->device);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -628,6 +653,7 @@ dsasa_status dsasa_status_sync(dsasa_ctx* c) {
     if (s & ST_INPUT) return fail(c, DSASA_ERR_INPUT, "non-finite coordinate or radius (status 0x%x)", s);
     if (s & (ST_CAND_OVF | ST_TRI_OVF | ST_GRID_OVF | ST_EXPORT_OVF))
         return fail(c, DSASA_ERR_CAPACITY, "a fixed per-atom or grid capacity was exceeded (status 0x%x)", s);
+    if (s & ST_CHECK) return fail(c, DSASA_ERR_CHECK, "a device bounds check failed (checked build; status 0x%x)", s);
     if (s & (ST_UNRESOLVED | ST_BADCELL))
         return fail(c, DSASA_ERR_UNRESOLVED, "an exact predicate or a cell could not be resolved (status 0x%x)", s);
     return fail(c, DSASA_ERR_DEGENERATE, "an exactly degenerate configuration was met (status 0x%x)", s);
@@ -646,6 +672,7 @@ dsasa_status dsasa_deferred_count(dsasa_ctx* c, int64_t* deferred) {
 
 dsasa_status dsasa_export_complex(dsasa_ctx* c, const double* coords, const double* radii, double probe, int64_t n,
                                   int32_t* records, int64_t max_records, int64_t* n_records) {
+    NvtxRange nvtx_range("dsasa_export_complex");
     if (!c || !n_records) return DSASA_ERR_ARG;
     *n_records = 0;
     if (!records && max_records > 0) return fail(c, DSASA_ERR_ARG, "records is NULL");

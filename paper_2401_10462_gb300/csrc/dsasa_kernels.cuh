@@ -48,8 +48,24 @@ enum : int {
     ST_BADCELL = 16,      // inconsistent cell structure detected (atom output set to NaN)
     ST_INPUT = 32,        // non-finite input
     ST_EXPORT_OVF = 64,   // complex export buffer too small
-    ST_GRID_OVF = 128     // cell grid larger than its capacity
+    ST_GRID_OVF = 128,    // cell grid larger than its capacity
+    ST_CHECK = 256        // a bounds check of the checked build failed (the access was redirected)
 };
+
+// The checked build (-DDSASA_CHECKED): every data-dependent index into a global array of
+// atoms (sorted positions, neighbour entries, plane owners, work lists) is verified on the
+// device.  A bad index sets ST_CHECK and is replaced by 0, so the access stays inside the
+// array; the results of that call are then not to be used.  The normal build checks nothing.
+#ifdef DSASA_CHECKED
+__device__ __forceinline__ int ds_checked(int idx, int lim, int* status) {
+    if ((unsigned)idx < (unsigned)lim) return idx;
+    atomicOr(status, ST_CHECK);
+    return 0;
+}
+#define DS_IDX(idx, lim, status) ds_checked((idx), (lim), (status))
+#else
+#define DS_IDX(idx, lim, status) (idx)
+#endif
 
 // cell grid of one molecule: cells of edge `cell` starting at `lo`, cell id = base + local
 struct MolGrid {
@@ -196,6 +212,9 @@ cudaError_t launch_verlet_check_batch(const double* xyz, const double* radii, co
 cudaError_t launch_sr(const SRArgs& a, cudaStream_t s);
 cudaError_t launch_atoms_f32(const AtomArgs& a, bool grad, cudaStream_t s);
 cudaError_t launch_atoms_f64(const AtomArgs& a, bool grad, cudaStream_t s);
+// whether n atoms fit one wave of the fused cell + classification kernel (mixed / FP64 form)
+bool atoms_one_wave_f32(int n);
+bool atoms_one_wave_f64(int n);
 size_t scan_scratch_ints(int max_cells);
 size_t cell_record_bytes();
 

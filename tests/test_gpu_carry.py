@@ -72,7 +72,7 @@ def test_carried_complex_is_the_oracles(api, torch_cuda, orc, gen, precision):
     torch = torch_cuda
     m = gen.globule(3000, 4)
     rng = np.random.default_rng(7)
-    ctx = api.Context(precision=precision, skin=1.0)
+    ctx = api.Context(precision=precision, skin=1.0, carry=2)
     r = torch.as_tensor(m.radii, device="cuda")
     x = m.coords.copy()
     ctx.export_complex(torch.as_tensor(x, device="cuda"), r)   # builds the lists and the cells
@@ -95,8 +95,8 @@ def test_carry_matches_fresh_cells(api, torch_cuda, orc, gen):
     torch = torch_cuda
     m = gen.globule(2000, 9)
     rng = np.random.default_rng(5)
-    carry = api.Context(skin=1.0)
-    plain = api.Context(skin=1.0, carry=False)
+    carry = api.Context(skin=1.0, carry=2)
+    plain = api.Context(skin=1.0, carry=0)
     fresh = api.Context()
     x = m.coords.copy()
     for step in range(11):
@@ -126,7 +126,7 @@ def test_same_positions_carry_every_cell(api, torch_cuda, orc, gen):
     atom with a cell carries it; areas equal the first call's up to summation order."""
     torch = torch_cuda
     m = gen.globule(1500, 3)
-    ctx = api.Context(skin=0.8)
+    ctx = api.Context(skin=0.8, carry=2)
     a0, g0, nc0, _ = _run(torch, ctx, m.coords, m.radii)
     a1, g1, nc1, reused = _run(torch, ctx, m.coords, m.radii)
     assert nc0 == 0 and reused
@@ -150,7 +150,7 @@ def test_degenerate_inputs_carry_consistently(api, torch_cuda, orc, case):
         f = np.array([[3.5, 0, 0], [-3.5, 0, 0], [0, 3.5, 0], [0, -3.5, 0], [0, 0, 3.5], [0, 0, -3.5]])
         x = np.concatenate([[[0.0, 0.0, 0.0]], c, f]) + np.array([4.0, -2.0, 1.5])
         r = np.concatenate([[1.2], np.full(8, 1.5), np.full(6, 1.7)])
-    ctx = api.Context(skin=0.5)
+    ctx = api.Context(skin=0.5, carry=2)
     xt, rt = torch.as_tensor(x, device="cuda"), torch.as_tensor(r, device="cuda")
     for call in range(2):
         rec = ctx.export_complex(xt, rt).cpu().numpy()
@@ -165,7 +165,7 @@ def test_rebuild_carries_nothing(api, torch_cuda, gen):
     cell afresh; so does a context with carrying off."""
     torch = torch_cuda
     m = gen.globule(1000, 2)
-    ctx = api.Context(skin=1.0)
+    ctx = api.Context(skin=1.0, carry=2)
     x = m.coords.copy()
     _run(torch, ctx, x, m.radii)
     x[10] += np.array([0.0, 0.7, 0.0])
@@ -174,3 +174,27 @@ def test_rebuild_carries_nothing(api, torch_cuda, gen):
     _, _, nc, reused = _run(torch, ctx, x, m.radii)
     assert reused and nc > 0
     ctx.close()
+
+
+def test_default_policy_carries_beyond_one_wave(api, torch_cuda, gen):
+    """carry = 1 (the default): a molecule that fits one wave of the fused cell kernel keeps
+    the fused kernel (no carried cells); a larger one carries, with results as a fresh build's."""
+    torch = torch_cuda
+    rng = np.random.default_rng(9)
+    small = gen.globule(2000, 1)
+    ctx = api.Context(skin=1.0)
+    _run(torch, ctx, small.coords, small.radii)
+    _, _, nc, reused = _run(torch, ctx, small.coords + rng.normal(scale=0.01, size=small.coords.shape), small.radii)
+    assert reused and nc == 0
+    ctx.close()
+    big = gen.make("globule", 12000, 3)
+    ctx, fresh = api.Context(skin=1.0), api.Context()
+    _run(torch, ctx, big.coords, big.radii)
+    x = big.coords + rng.normal(scale=0.01, size=big.coords.shape)
+    a, g, nc, reused = _run(torch, ctx, x, big.radii)
+    af, gf, _, _ = _run(torch, fresh, x, big.radii)
+    assert reused and nc >= 0.5 * big.n, nc
+    assert np.all(np.abs(a - af) <= 1e-5 * np.maximum(af, 1.0))
+    _grad_close(g, gf)
+    ctx.close()
+    fresh.close()
