@@ -371,7 +371,8 @@ def run_gpu(args):
                      "note": "call time includes the cell-list build; 9 FP32 flop per point-neighbour test"}
     ctx.close()
 
-    # e2e through the C ABI with pinned host buffers (copies inside the timed region)
+    # e2e through the C ABI with pinned host buffers: the kernels read the inputs and write the
+    # outputs in host memory over the CPU-GPU link (inside the timed region, with the sync)
     ctx = api.Context(device=local, stream=stream)
     hx = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     hr = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
@@ -407,7 +408,9 @@ def run_gpu(args):
         "roofline_terms": roofline_terms,
         "peaks_measured": pk,
         "phase_ms": {"mixed": ph_mixed, "fp64": ph_fp64},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 32 * n},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 32 * n,
+                "transfer": "pinned host buffers read and written in place by the kernels over the CPU-GPU "
+                            "link (dsasa_compute_host); wall clock per call including the synchronisation"},
         "gpu_launches": launches_mixed,
         "clocks": clk.summary(),
     }

@@ -224,9 +224,12 @@ dsasa_status dsasa_compute_batch_resident(dsasa_ctx* ctx, dsasa_arena* arena, in
  * 1 if its lists were reused (0: rebuilt or none). */
 dsasa_status dsasa_batch_reused(dsasa_ctx* ctx, int n_mol, int32_t* reused_host);
 
-/* End-to-end convenience on HOST buffers: copies coords/radii/weights to the device, runs
- * dsasa_compute_vjp, copies areas (and grad if grad_host != NULL) back and synchronises
- * the stream.  Host buffers may be pageable or pinned; weights_host may be NULL. */
+/* End-to-end convenience on HOST buffers: runs dsasa_compute_vjp on coords/radii/weights in
+ * host memory, leaves areas (and grad if grad_host != NULL) in host memory and synchronises
+ * the stream.  When every buffer is pinned (page-locked, hence mapped into the device's
+ * address space) the kernels read and write them in place over the CPU-GPU link, with no
+ * copy; otherwise (pageable memory) the inputs are copied to device staging buffers and the
+ * outputs back.  weights_host may be NULL. */
 dsasa_status dsasa_compute_host(dsasa_ctx* ctx, const double* coords_host, const double* radii_host,
                                 double probe, int64_t n, const double* weights_host,
                                 double* areas_host, double* grad_host);

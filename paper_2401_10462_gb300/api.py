@@ -280,7 +280,9 @@ class Context:
         return out[:n_mol].astype(bool)
 
     def compute_host(self, coords, radii, weights=None, grad: bool = True, probe: float = PROBE, out=None):
-        """dsasa_compute_host on numpy buffers: copies in, computes, copies out, synchronises."""
+        """dsasa_compute_host on numpy buffers, synchronised.  Buffers in pinned memory (e.g.
+        numpy views of torch tensors made with pin_memory=True) are read and written in place
+        by the kernels; pageable ones are copied through device staging buffers."""
         xyz = np.ascontiguousarray(coords, dtype=np.float64)
         r = np.ascontiguousarray(radii, dtype=np.float64)
         n = xyz.shape[0]

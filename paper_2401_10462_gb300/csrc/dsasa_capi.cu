@@ -608,6 +608,32 @@ dsasa_status dsasa_compute_host(dsasa_ctx* c, const double* coords_host, const d
     dsasa_status st = check_common(c, coords_host, radii_host, probe, n, areas_host);
     if (st != DSASA_OK || n == 0) return st;
     cudaError_t e;
+    // Pinned (page-locked) host buffers are mapped into the device's address space: the
+    // kernels then read the inputs and write the outputs in host memory themselves, over the
+    // coherent CPU-GPU link, with no staging copy either way.  Pageable buffers are copied.
+    auto mapped = [](const void* h) -> void* {
+        if (!h) return nullptr;
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+    };
+    {
+        const double* dx = (const double*)mapped(coords_host);
+        const double* dr = (const double*)mapped(radii_host);
+        const double* dw = (const double*)mapped(weights_host);
+        double* da = (double*)mapped(areas_host);
+        double* dg = (double*)mapped(grad_host);
+        if (dx && dr && da && (!weights_host || dw) && (!grad_host || dg)) {
+            st = run(c, dx, dr, probe, n, 1, nullptr, dw, da, dg, nullptr, 0);
+            if (st != DSASA_OK) return st;
+            e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+            return DSASA_OK;
+        }
+    }
     if (n > c->cap_host) {
         if (c->cfg.max_atoms > 0 && n > c->cfg.max_atoms)
             return fail(c, DSASA_ERR_CAPACITY, "n=%lld exceeds max_atoms", (long long)n);

@@ -256,6 +256,37 @@ def test_host_entry_point_matches_device(api, torch_cuda, gen):
     assert np.array_equal(a_h, a_d) and np.array_equal(g_h, g_d)
 
 
+@pytest.mark.parametrize("case", ["pinned", "pinned-weights", "pinned-skin", "pinned-in-pageable-out"])
+def test_host_entry_point_in_place_on_pinned_buffers(api, torch_cuda, gen, case):
+    """Pinned host buffers are read and written in place by the kernels (no staging copy);
+    the results equal the device entry point's bit for bit, also with weights, with Verlet
+    lists (the list check reads the host coordinates) and with pageable outputs (copy path)."""
+    torch = torch_cuda
+    m = gen.globule(2000, 5)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hx, hr = pin(m.coords), pin(m.radii)
+    w = pin(np.linspace(0.5, 1.5, m.n)) if case == "pinned-weights" else None
+    if case == "pinned-in-pageable-out":
+        ha, hg = np.empty(m.n), np.empty((m.n, 3))
+    else:
+        ha, hg = pin(np.zeros(m.n)), pin(np.zeros((m.n, 3)))
+    ctx = api.Context(skin=1.0 if case == "pinned-skin" else 0.0)
+    ref = api.Context()
+    steps = [m.coords, m.coords + np.random.default_rng(2).normal(scale=0.01, size=m.coords.shape)]
+    for xs in steps if case == "pinned-skin" else steps[:1]:
+        hx[:] = xs
+        ctx.compute_host(hx, hr, weights=w, out=(ha, hg))
+        a = torch.empty(m.n, dtype=torch.float64, device="cuda")
+        g = torch.empty((m.n, 3), dtype=torch.float64, device="cuda")
+        ref.compute(_dev(torch, xs), _dev(torch, m.radii), a, g, weights=None if w is None else _dev(torch, w))
+        ref.status_sync()
+        assert np.array_equal(ha, a.cpu().numpy()) and np.array_equal(hg, g.cpu().numpy())
+    if case == "pinned-skin":
+        assert ctx.lists_reused()
+    ctx.close()
+    ref.close()
+
+
 def test_batch_equals_separate(api, torch_cuda, gen):
     torch = torch_cuda
     mols = [gen.globule(300, 1), gen.rna(640, 2), gen.globule(1000, 3)]
