@@ -461,6 +461,34 @@ template <class SM, class R = typename SM::Real> __device__ __forceinline__ P3<R
     return {S->pq[e][0], S->pq[e][1], S->pq[e][2]};
 }
 
+// ------------------------------------------------------------------ the initial cube
+// Corner t of the cube of the 6 ghost planes (bit 0 / 1 / 2 of t: the -x / -y / -z side): the
+// triangle of its three planes, oriented like every cell vertex (positive orientation).
+__host__ __device__ constexpr int cube_corner_plane(int t, int k) {
+    const int sx = (t & 1) ? -1 : 1, sy = (t & 2) ? -1 : 1, sz = (t & 4) ? -1 : 1;
+    const int px = sx > 0 ? 0 : 1, py = sy > 0 ? 2 : 3, pz = sz > 0 ? 4 : 5;
+    const bool even = sx * sy * sz > 0;
+    return k == 0 ? (even ? px : py) : (k == 1 ? (even ? py : px) : pz);
+}
+// The corner across edge k (from plane k to plane k + 1 of the triangle) of every corner,
+// one byte per corner: the cube's adjacency, computed at compile time.
+__host__ __device__ constexpr unsigned long long cube_adjacency(int k) {
+    unsigned long long packed = 0;
+    for (int t = 0; t < 8; ++t) {
+        const int a = cube_corner_plane(t, k), b = cube_corner_plane(t, (k + 1) % 3);
+        for (int t2 = 0; t2 < 8; ++t2)
+            for (int k2 = 0; k2 < 3; ++k2)
+                if (cube_corner_plane(t2, k2) == b && cube_corner_plane(t2, (k2 + 1) % 3) == a)
+                    packed |= (unsigned long long)t2 << (8 * t);
+    }
+    return packed;
+}
+constexpr unsigned long long CUBE_ADJ0 = cube_adjacency(0), CUBE_ADJ1 = cube_adjacency(1),
+                             CUBE_ADJ2 = cube_adjacency(2);
+static_assert(CUBE_ADJ0 == 0x0302010007060504ull && CUBE_ADJ1 == 0x0507040602000301ull &&
+                  CUBE_ADJ2 == 0x0604070501030002ull,
+              "every edge of the cube's triangulation has exactly one neighbour across it");
+
 // ------------------------------------------------------------------ carried cells
 // The incremental update of C across MD steps.  On a call that reuses the neighbour lists
 // (every atom within half the skin of its last rebuild), the cell that the previous call
@@ -1011,30 +1039,18 @@ __global__ void __launch_bounds__(warps_of(PHX) * 32, minb(PHX)) k_atoms(AtomArg
         // ---------------- initial cell: the cube of the 6 ghost planes (8 vertices)
         for (int t = lane; t < NT; t += 32) {
             uchar4 v = make_uchar4(NONE, NONE, NONE, 0);
-            if (t < 8) {
-                int sx = (t & 1) ? -1 : 1, sy = (t & 2) ? -1 : 1, sz = (t & 4) ? -1 : 1;
-                uint8_t px = sx > 0 ? 0 : 1, py = sy > 0 ? 2 : 3, pz = sz > 0 ? 4 : 5;
-                v = (sx * sy * sz > 0) ? make_uchar4(px, py, pz, 0) : make_uchar4(py, px, pz, 0);
-            }
+            if (t < 8)
+                v = make_uchar4((uint8_t)cube_corner_plane(t, 0), (uint8_t)cube_corner_plane(t, 1),
+                                (uint8_t)cube_corner_plane(t, 2), 0);
             S->tv[t] = v;
             S->rem[t] = 0;
             S->kf[t] = 0;
             S->tf[t] = 0;
         }
         if (lane == 0) { S->hw = 8; S->nfree = 0; S->bad = 0; }
-        __syncwarp();
         if (lane < 8) {
-            uchar4 v = S->tv[lane];
-            uchar4 adj = make_uchar4(NONE, NONE, NONE, 0);
-            for (int k = 0; k < 3; ++k) {
-                uint8_t a = tv_get(v, k), b = tv_get(v, (k + 1) % 3);
-                for (int t2 = 0; t2 < 8; ++t2) {
-                    uchar4 w = S->tv[t2];
-                    for (int k2 = 0; k2 < 3; ++k2)
-                        if (tv_get(w, k2) == b && tv_get(w, (k2 + 1) % 3) == a) ((uint8_t*)&adj)[k] = (uint8_t)t2;
-                }
-            }
-            S->ta[lane] = adj;
+            const int sh = 8 * lane;
+            S->ta[lane] = make_uchar4((uint8_t)(CUBE_ADJ0 >> sh), (uint8_t)(CUBE_ADJ1 >> sh), (uint8_t)(CUBE_ADJ2 >> sh), 0);
         }
         if (lane < NG) S->start[lane] = (lane & 1) ? 7 : 0;   // +x,+y,+z at corner 0; -x,-y,-z at 7
         __syncwarp();
