@@ -67,17 +67,18 @@ typedef enum {
  *                 sqrt, atan2) in FP32; the radius quantities (R_i, R_i^2, R_i^2 - R_j^2)
  *                 enter the area terms as float-float pairs and all area terms of an atom are
  *                 one float-float warp sum; the per-atom constants (multiples of 2 pi R_i^2)
- *                 are added once in FP64.  The gradient is summed in FP32.  Predicates are
- *                 filtered in FP32, then FP64, then decided by exact expansions.
- *                 The gradient contributions of an atom are summed in float-float (the result
- *                 does not depend on their order).  The one FP32 quantity that cancels
- *                 without bound, the height of a triangle's triple points over the plane of
- *                 its centres (R_i^2 - |z|^2), is taken from the float64 coordinates when its
+ *                 are added once in FP64.  The gradient contributions of an atom are summed
+ *                 in int64 fixed point (2^-40; each FP32 term rounded once, the sum exact and
+ *                 independent of its order).  Predicates are filtered in FP32, then FP64, then
+ *                 decided by exact expansions.  The one FP32 quantity that cancels without
+ *                 bound, the height of a triangle's triple points over the plane of its
+ *                 centres (R_i^2 - |z|^2), is taken from the float64 coordinates when its
  *                 square is below 0.01 R_i^2: the lens gradient is linear in it.
  *                 Limit: the neighbour vectors enter the terms rounded to float, which leaves
- *                 an absolute gradient error of about 1e-5 (A^2 / A) per atom; an atom whose
- *                 gradient is below about 0.02 (nearly buried, or a sliver) can therefore miss
- *                 a 1e-3 relative bound with a 1e-2 floor.  DSASA_FP64 has no such limit.
+ *                 an absolute gradient error of up to about 3e-5 (A^2 / A) per atom; an atom
+ *                 whose gradient is below about 0.03 (nearly buried, or a sliver) can
+ *                 therefore miss a 1e-3 relative bound with a 1e-2 floor.  DSASA_FP64 has no
+ *                 such limit.
  *   DSASA_FP64  - every term in FP64; predicates filtered in FP64, then exact. */
 enum { DSASA_MIXED = 0, DSASA_FP64 = 1 };
 
