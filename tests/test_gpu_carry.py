@@ -198,3 +198,71 @@ def test_default_policy_carries_beyond_one_wave(api, torch_cuda, gen):
     _grad_close(g, gf)
     ctx.close()
     fresh.close()
+
+
+def _large_ball_in_shell(m=40, zcut=-2.0):
+    """A large ball inside a partly open shell of small ones (its cell needs the 128 / 128
+    pass), in a field of small balls around it."""
+    import math
+    rng = np.random.default_rng(3)
+    idx = np.arange(m) + 0.5
+    z = 1 - 2 * idx / m
+    rr = np.sqrt(1 - z * z)
+    ang = math.pi * (1 + 5 ** 0.5) * idx
+    shell = 5.2 * np.stack([rr * np.cos(ang), rr * np.sin(ang), z], 1) + 1e-5 * rng.normal(size=(m, 3))
+    shell = shell[z > zcut]
+    return np.concatenate([np.zeros((1, 3)) + 1e-6, shell]), np.concatenate([[3.6], np.full(len(shell), 1.2)])
+
+
+def test_deferred_cell_through_carried_steps(api, torch_cuda, orc):
+    """An atom whose cell needs the large-capacity pass, over list-reusing steps with carrying
+    on: it is never carried (the redo list sends it to the cell kernel, which defers it), the
+    other cells carry, and the complex stays the oracle's."""
+    torch = torch_cuda
+    x0, r = _large_ball_in_shell()
+    ctx = api.Context(skin=0.6, carry=2)
+    rng = np.random.default_rng(11)
+    x = x0.copy()
+    for step in range(3):
+        if step:
+            x = x + rng.normal(scale=0.005, size=x.shape)
+        rec = ctx.export_complex(torch.as_tensor(x, device="cuda"), torch.as_tensor(r, device="cuda")).cpu().numpy()
+        carried = ctx.cells_carried()
+        assert ctx.deferred_count() >= 1
+        ctx.status_sync()
+        _check_against_oracle(orc, rec, x, r)
+        if step:
+            assert 0 < carried < len(r)
+    ctx.close()
+
+
+def test_volumes_through_carried_cells(api, torch_cuda, gen):
+    """The volume kernel reads the carried cells' records: volumes and their gradient over
+    carried steps equal those of a context without lists."""
+    torch = torch_cuda
+    m = gen.globule(2500, 6)
+    ctx, fresh = api.Context(skin=1.0, carry=2), api.Context()
+    rng = np.random.default_rng(12)
+    x = m.coords.copy()
+    rt = torch.as_tensor(m.radii, device="cuda")
+    for step in range(3):
+        if step:
+            x = x + rng.normal(scale=0.01, size=x.shape)
+        xt = torch.as_tensor(x, device="cuda")
+        out = []
+        for c in (ctx, fresh):
+            a = torch.empty(m.n, dtype=torch.float64, device="cuda")
+            v = torch.empty(m.n, dtype=torch.float64, device="cuda")
+            vg = torch.empty((m.n, 3), dtype=torch.float64, device="cuda")
+            c.compute_volume(xt, rt, a, v, vol_grad_out=vg)
+            c.status_sync()
+            out.append((a.cpu().numpy(), v.cpu().numpy(), vg.cpu().numpy()))
+        if step:
+            assert ctx.cells_carried() > 0.5 * m.n
+        (a1, v1, g1), (a0, v0, g0) = out
+        assert np.all(np.abs(a1 - a0) <= 1e-5 * np.maximum(a0, 1.0))
+        assert np.all(np.abs(v1 - v0) <= 1e-5 * np.maximum(v0, 1.0))
+        assert abs(v1.sum() - v0.sum()) <= 1e-9 * v0.sum()
+        _grad_close(g1, g0)
+    ctx.close()
+    fresh.close()
