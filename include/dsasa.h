@@ -186,8 +186,8 @@ dsasa_status dsasa_compute_batch(dsasa_ctx* ctx, int n_mol, const int64_t* atom_
                                  const double* coords, const double* radii, double probe,
                                  const double* area_weights, double* areas_out, double* grad_out);
 
-/* Resident Verlet lists for serving (no paper counterpart; the north star's "neighbour lists
- * resident on the device across requests"): an arena of capacity_atoms atom slots on
+/* Resident Verlet lists for serving (no paper counterpart: neighbour lists kept on the
+ * device across requests): an arena of capacity_atoms atom slots on
  * `device` holding, per atom, its candidate list (atoms within R_i + R_j + skin at the
  * list's build, molecule-local indices), the list length and the coordinates and radius
  * at the build.  The caller assigns each resident molecule a slot range [base, base + n)
