@@ -516,7 +516,7 @@ def host_info():
 
 
 def cpu_baseline(m):
-    """The oracle as it stands on the GPU machine's host: single-threaded end to end (triangulation
+    """The oracle as it stands on the host cores of the machine that runs the GPU: single-threaded end to end (triangulation
     + complex + areas + gradient) on the 304- and 5,000-atom globules and a 20,000-atom one,
     and its area and gradient stage on all cores (OpenMP; the triangulation stays serial);
     1,000,000 atoms extrapolated as n log n from the 20,000-atom time.  Returns the record and

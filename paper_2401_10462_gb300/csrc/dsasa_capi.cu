@@ -154,7 +154,7 @@ dsasa_status ensure(dsasa_ctx* c, int64_t n, int64_t n_mol) {
         return fail(c, DSASA_ERR_CAPACITY, "n=%lld molecules=%lld exceed the fixed capacity (max_atoms=%lld)",
                     (long long)n, (long long)n_mol, (long long)c->cfg.max_atoms);
     if (n > 0x3fffffff || need_cells > 0x7ffffff0)
-        return fail(c, DSASA_ERR_CAPACITY, "n=%lld is beyond the 32-bit index range of this build", (long long)n);
+        return fail(c, DSASA_ERR_CAPACITY, "n=%lld is beyond the 32-bit index range of the kernels", (long long)n);
     // the stream may still use the old buffers
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");

@@ -6,7 +6,7 @@
 //
 // Built into its own library (libdsasa_peaks.so) so that the product library carries no
 // benchmark code; bench.py calls it once per run and reports the measured roofs beside the
-// measured HBM and tensor peaks.
+// HBM copy and tensor peaks recorded for the machine (MEASURED_PEAKS.json).
 #include <cuda_runtime.h>
 
 #include <stdint.h>

@@ -130,7 +130,7 @@ def test_triangle_term_against_mc_directly(orc):
 
 
 def test_gauss_bonnet_pinned_by_closed_forms(orc):
-    # the checker itself: isolated and two-sphere closed forms
+    # the Gauss-Bonnet cross-check itself: isolated and two-sphere closed forms
     a, bad = orc.gauss_bonnet(np.zeros((1, 3)), np.array([1.55]))
     assert a[0] == pytest.approx(4 * math.pi * (1.55 + P) ** 2, rel=1e-14)
     xyz = np.array([[0, 0, 0], [2.5, 1.0, 0.0]])
