@@ -56,7 +56,7 @@ _lib.dsasa_compute_batch_resident.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POI
                                               ctypes.POINTER(ctypes.c_int64), _vp, _vp, ctypes.c_double, _vp, _vp,
                                               _vp, _vp]
 _lib.dsasa_batch_reused.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
-_lib.dsasa_compute_host.argtypes = [_vp, _dp, _dp, ctypes.c_double, _i64, _dp, _dp, _dp]
+_lib.dsasa_compute_host.argtypes = [_vp, _vp, _vp, ctypes.c_double, _i64, _vp, _vp, _vp]
 _lib.dsasa_status_sync.argtypes = [_vp]
 _lib.dsasa_deferred_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
 _lib.dsasa_set_timing.argtypes = [_vp, ctypes.c_int]
@@ -292,8 +292,12 @@ class Context:
             g = np.empty((n, 3)) if grad else None
         else:
             a, g = out
+            for arr, shape in ((a, (n,)), (g, (n, 3))):
+                if arr is not None and (arr.dtype != np.float64 or arr.shape != shape or not arr.flags.c_contiguous
+                                        or not arr.flags.writeable):
+                    raise ValueError(f"out arrays must be writeable C-contiguous float64 of shape {shape}")
         self._sync_stream()
-        dp = lambda x: None if x is None else x.ctypes.data_as(_dp)
+        dp = lambda x: None if x is None else x.ctypes.data   # the address (cheaper than data_as)
         self._raise(_lib.dsasa_compute_host(self._h, dp(xyz), dp(r), float(probe), n, dp(w), dp(a), dp(g)))
         return a, g
 
