@@ -30,6 +30,7 @@ request at a time, so that the status names the request that caused it.
 """
 from __future__ import annotations
 
+import gc
 import time
 from dataclasses import dataclass, field
 
@@ -186,6 +187,8 @@ class Server:
                 if self.with_grad:
                     r.grad = slot.h_grad.numpy()[off[k]:off[k + 1]].copy()
                 t_now = t_now if t_now is not None else time.perf_counter() - t0
+                if r.done is None:
+                    self._n_done += 1
                 r.done = t_now
                 slot.pending.discard(k)
         if slot.pending or not slot.event.query():
@@ -219,7 +222,17 @@ class Server:
 
     def run(self, requests, realtime: bool = True):
         """Serve the requests (sorted by arrival).  With realtime=False every request is
-        available at t = 0 (saturated throughput)."""
+        available at t = 0 (saturated throughput).  Python's cyclic garbage collector is paused
+        while the requests are served (a collection would stall the polling loop)."""
+        gc_was_enabled = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(requests, realtime)
+        finally:
+            if gc_was_enabled:
+                gc.enable()
+
+    def _run(self, requests, realtime: bool):
         reqs = sorted(requests, key=lambda r: r.arrival)
         for r in reqs:
             if r.n > self.slot_atoms:
@@ -227,6 +240,7 @@ class Server:
             if r.n == 0:
                 raise ValueError(f"request {r.rid} has no atoms")
         queue, nxt, done = [], 0, 0
+        self._n_done = sum(1 for r in reqs if r.done is not None)   # completions, counted as they come
         t0 = time.perf_counter()
         while done < len(reqs):
             now = time.perf_counter() - t0
@@ -237,7 +251,7 @@ class Server:
             for slot in self.slots:
                 if slot.event is not None and self._collect(slot, t0):
                     progressed = True
-            done = sum(1 for r in reqs if r.done is not None)
+            done = self._n_done
             for slot in self.slots:
                 if slot.event is None and queue:
                     # first come, first served while the atoms fit; a request whose molecule is
