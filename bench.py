@@ -414,19 +414,33 @@ def run_gpu(args):
         "gpu_launches": launches_mixed,
         "clocks": clk.summary(),
     }
+    # the further workloads and the CPU legs: a failure of one of them is reported in its own
+    # key, and the headline line is still printed
+    def leg(name, fn):
+        try:
+            line[name] = fn()
+        except Exception as ex:   # noqa: BLE001 - reported, not swallowed
+            line[name] = {"error": f"{type(ex).__name__}: {ex}"}
+
     if rank == 0 and ws == 1 and not args.quick:
-        line["capsid"] = capsid_measure(args, tm, wm, pk)
-        line["trajectory"] = trajectory_measure(args, local)
-        with ClockSampler(local) as sclk:
-            line["serving"] = serving_measure(4096, 32, loads=(0.5, 0.8, 0.95))
-        line["serving"]["clocks"] = sclk.summary()
+        leg("capsid", lambda: capsid_measure(args, tm, wm, pk))
+        leg("trajectory", lambda: trajectory_measure(args, local))
+
+        def serving():
+            with ClockSampler(local) as sclk:
+                out = serving_measure(4096, 32, loads=(0.5, 0.8, 0.95))
+            out["clocks"] = sclk.summary()
+            return out
+        leg("serving", serving)
     if rank == 0 and not args.no_cpu_baseline:
-        base, ref = cpu_baseline(m)
-        line["cpu_baseline"] = base
-        line["accuracy_vs_oracle"] = {"mixed": accuracy(ref[0], ref[1], a_mix.cpu().numpy(), g_mix.cpu().numpy()),
-                                      "fp64": accuracy(ref[0], ref[1], a_64.cpu().numpy(), g_64.cpu().numpy()),
-                                      "tolerances": "per atom |dA| <= 1e-4 max(A, 1 A^2); total 1e-6; "
-                                                    "|dg| <= 1e-3 max(|g|, 1e-2)"}
+        def cpu_legs():
+            base, ref = cpu_baseline(m)
+            line["accuracy_vs_oracle"] = {
+                "mixed": accuracy(ref[0], ref[1], a_mix.cpu().numpy(), g_mix.cpu().numpy()),
+                "fp64": accuracy(ref[0], ref[1], a_64.cpu().numpy(), g_64.cpu().numpy()),
+                "tolerances": "per atom |dA| <= 1e-4 max(A, 1 A^2); total 1e-6; |dg| <= 1e-3 max(|g|, 1e-2)"}
+            return base
+        leg("cpu_baseline", cpu_legs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
