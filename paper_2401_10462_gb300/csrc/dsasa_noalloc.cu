@@ -3,7 +3,7 @@
 // Some callers cannot let a library call cudaMalloc: a host application (an MD engine, a
 // plugin host) that provisions a fixed device-memory budget up front and accounts for every
 // byte, a process whose memory is owned by another framework's pool allocator, or a
-// latency-critical loop that must never hit the driver's allocator.  This entry point serves
+// latency-critical loop that must never reach the CUDA allocator.  This entry point serves
 // them: its scratch (cell list, sorted atom copies, status word) lives in one file-scope
 // __device__ array of fixed size, so the call allocates nothing; the caller still passes its
 // own input and output buffers.
